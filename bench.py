@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the FAS/fast-sweeping moment solver on GB300.
+
+One step = one NMG V-cycle of Algorithm 2 (FS smoothing on every level, residual, restriction,
+coarse right-hand side, coarse-grid update), the mass correction and the residual norm, on the
+lid-driven cavity 256x256, M = 10 (286 moments), BGK, Kn = 0.01, lid velocity 0.5, second-order
+van Albada reconstruction, 6 levels (coarsest 8x8), s1 = s2 = 2, s3 = 4.
+
+metric: cell-moment updates per second = 4 sweeps x cells x N_M per FS step, summed over the
+FS steps of every level in the timed cycles (residual evaluations are not counted).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload lid256|lid32|heat512]
+
+With --impl reference the CPU oracle (plain serial C) is timed on the host on a bounded sample
+of the same workload.  Multi-GPU runs (torchrun) solve one independent replica per GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (nx, M, Kn, walls, model, Pr, order, slope, levels, description)
+    "lid256": dict(nx=256, M=10, Kn=0.01, lid=0.5, heat=None, model=0, Pr=2 / 3, order=2, slope=2, levels=6,
+                   desc="lid-driven cavity 256x256, M=10 (286 moments), BGK, Kn=0.01, lid 0.5, "
+                        "2nd-order van Albada, 6-level FAS V-cycle (s1,s2,s3)=(2,2,4)"),
+    "lid32": dict(nx=32, M=5, Kn=0.1, lid=0.1, heat=None, model=0, Pr=2 / 3, order=1, slope=0, levels=3,
+                  desc="lid-driven cavity 32x32, M=5 (56 moments), BGK, Kn=0.1, lid 0.1, first order, "
+                       "3-level FAS V-cycle (2,2,4)"),
+    "heat512": dict(nx=512, M=8, Kn=0.05, lid=0.0, heat=2.0, model=1, Pr=2 / 3, order=2, slope=2, levels=7,
+                    desc="bottom-heated cavity 512x512, M=8 (165 moments), Shakhov Pr=2/3, Kn=0.05, "
+                         "theta_bottom=2, 2nd-order van Albada, 7-level FAS V-cycle (2,2,4)"),
+}
+
+
+def nmom(M):
+    return (M + 1) * (M + 2) * (M + 3) // 6
+
+
+def walls_of(w):
+    walls = [((0.0, 0.0, 0.0), 1.0, 1.0) for _ in range(4)]
+    if w["lid"]:
+        walls[2] = ((w["lid"], 0.0, 0.0), 1.0, 1.0)
+    if w["heat"]:
+        walls[0] = ((0.0, 0.0, 0.0), w["heat"], 1.0)
+    return walls
+
+
+def cycle_updates(w):
+    """cell-moment updates of one V-cycle: 4 FS steps (s1+s2 or s3) on every level."""
+    n = nmom(w["M"])
+    tot = 0
+    for l in range(w["levels"]):
+        cells = (w["nx"] >> (w["levels"] - 1 - l)) ** 2
+        steps = 4  # s1 + s2 = 2 + 2 on levels >= 1, s3 = 4 on level 0
+        tot += steps * 4 * cells * n
+    return tot
+
+
+def flops_per_update(M, order, has_r):
+    """Algorithmic FP64 flops of one cell update: T per basis transform (2 flops x 3 directions x
+    C(M+3,4) multiply-adds), 9 transforms + 80 flops per moment at second order (5 + 60 at first
+    order), one more transform when the level has a right-hand side r."""
+    T = 6 * math.comb(M + 3, 4)
+    n = nmom(M)
+    f = (9 * T + 80 * n) if order == 2 else (5 * T + 60 * n)
+    return f + (T if has_r else 0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def cpu_oracle_sample(w, level_shift: int, sweeps: int = 1):
+    """Time the CPU oracle (as it stands, serial) on directional sweeps D1 of one level of the
+    workload.  Returns (cell-moment updates/s, seconds, description)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+
+    oracle.build()
+    c = oracle.OrConfig()
+    c.nx = c.ny = w["nx"]
+    c.lx = c.ly = 1.0
+    c.levels = w["levels"]
+    c.M, c.Kn, c.model, c.Pr, c.omega, c.beta = w["M"], w["Kn"], w["model"], w["Pr"], 0.81, 1.0
+    c.order, c.slope, c.cfl = w["order"], w["slope"], 0.9
+    c.s1, c.s2, c.s3, c.gamma = 2, 2, 4, 1
+    for k, (u, th, chi) in enumerate(walls_of(w)):
+        for d in range(3):
+            c.wall_u[k][d] = u[d]
+        c.wall_theta[k], c.wall_chi[k] = th, chi
+    S = oracle.Solver(c)
+    lev = w["levels"] - 1 - level_shift
+    ny, nx = S.shape(lev)
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        S.sweep(lev, 1)
+    dt = time.perf_counter() - t0
+    upd = sweeps * nx * ny * nmom(w["M"])
+    return upd / dt, dt, f"{sweeps} directional sweep(s) D1 over the {nx}x{ny} level of the workload " \
+                         f"({nx * ny} cell updates), serial oracle"
+
+
+def run_reference(args, w):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    # each step: one D1 sweep over the second-finest level (same per-cell work as the finest)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, 1)
+    times, rates, desc = [], [], ""
+    for _ in range(args.steps):
+        r, dt, desc = cpu_oracle_sample(w, 1)
+        times.append(dt)
+        rates.append(r)
+    tot_upd = sum(r * t for r, t in zip(rates, times))
+    value = tot_upd / sum(times)
+    out = {
+        "impl": "reference", "metric": "cell-moment updates/s", "value": value, "unit": "cell-moment updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "cell-moment updates/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "cell-moment updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lid256", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2206_13164_gb300 import nrmg
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    S = nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
+                    Pr=w["Pr"], order=w["order"], slope=w["slope"], device=dev)
+    stream = S.stream
+    fp64_peak_meas = nrmg.peak_fma(0, 2048, stream)
+    for _ in range(args.warmup):
+        S.fas_cycle()
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(props.uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    S.set_profiling(True)
+    S.fs_profile()  # reset
+    l0 = S.launches
+    with ClockSampler(gpu_id) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rel = None
+        for _ in range(args.steps):
+            rel = S.fas_cycle()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    launches = S.launches - l0
+    fs_ms, fs_n, u0, u1 = S.fs_profile()
+    S.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    upd = cycle_updates(w) * args.steps
+    value = upd * world / (ms * 1e-3)
+
+    # end to end through the public API: pinned host state -> device, one cycle, state -> host
+    P, F = S.get_state()
+    hP = torch.empty(P.shape, dtype=P.dtype, pin_memory=True)
+    hF = torch.empty(F.shape, dtype=F.dtype, pin_memory=True)
+    hP.copy_(P)
+    hF.copy_(F)
+    dP, dF = torch.empty_like(P), torch.empty_like(F)
+    oP = torch.empty(P.shape, dtype=P.dtype, pin_memory=True)
+    oF = torch.empty(F.shape, dtype=F.dtype, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            dP.copy_(hP, non_blocking=True)
+            dF.copy_(hF, non_blocking=True)
+        S.set_state(dP, dF)
+        S.fas_cycle()
+        P2, F2 = S.get_state()
+        with torch.cuda.stream(stream):
+            oP.copy_(P2, non_blocking=True)
+            oF.copy_(F2, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = cycle_updates(w) * e2e_steps * world / e2e_s
+    bytes_state = (hP.numel() + hF.numel()) * 8
+
+    # roofline of the dominant kernel (the persistent FS sweep kernel, all levels)
+    fl = u0 * flops_per_update(w["M"], w["order"], False) + u1 * flops_per_update(w["M"], w["order"], True)
+    achieved = fl / (fs_ms * 1e-3) / 1e12 if fs_ms > 0 else None
+    nsm = props.multi_processor_count
+    peak_nominal = nsm * 2 * 2 * 2.07e9 / 1e12  # 2 DFMA/clk/SM x 2 flops x 2070 MHz
+    clocks = clk.summary()
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            r, dt, desc = cpu_oracle_sample(w, 0 if w["nx"] <= 256 else 1)
+            cpu = {"value": r, "unit": "cell-moment updates/s", "cores": 1, "kind": "oracle",
+                   "sample": desc + f" ({dt:.1f} s)"}
+        out = {
+            "metric": "cell-moment updates/s", "value": value, "unit": "cell-moment updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "step": "one FAS V-cycle + mass correction + residual norm",
+                       "cell_moment_updates_per_step": cycle_updates(w),
+                       "l2": "inputs larger than L2 (finest-level coefficient array alone is "
+                             f"{w['nx'] ** 2 * ((nmom(w['M']) + 3) // 4 * 4) * 8 / 1e6:.0f} MB)",
+                       "parallelism": f"replicas x{world}", "rel_residual_after": rel},
+            "roofline": {"bound": "alu", "kernel": "fs_kernel (persistent FS sweep, all levels)",
+                         "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
+                         "frac": (achieved / peak_nominal) if achieved else None, "traffic": None,
+                         "peak_source": "derived: SMs x 2 DFMA/clk x 2 flops x 2070 MHz (FP64 pipe)",
+                         "fp64_fma_measured_tflops": fp64_peak_meas / 1e12,
+                         "fs_ms_per_step": fs_ms / args.steps, "fs_launches": fs_n,
+                         "flops_per_cell_update": flops_per_update(w["M"], w["order"], False)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "cell-moment updates/s", "h2d_bytes_per_step": bytes_state,
+                    "d2h_bytes_per_step": bytes_state, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * nrmg.h -- C ABI of the GB300 (sm_103a) nonlinear-multigrid solver for the
+ * regularized Hermite moment discretization of the BGK / Shakhov Boltzmann
+ * equation on a 2D cavity, after Hu & Li, "An efficient nonlinear multigrid
+ * solver for the simulation of rarefied gas cavity flow" (arXiv 2206.13164).
+ *
+ * Every compute step runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ * Units are nondimensional (molecular mass 1, velocities in sqrt(R T0)).
+ * Grid: nx x ny uniform cells on [0,lx] x [0,ly]; cell (i,j) has index
+ *   c = j*nx + i, i along x.  Levels are numbered as in Algorithm 2 of the
+ *   paper: level 0 is the coarsest grid, level levels-1 the finest; level l
+ *   has (nx >> (levels-1-l)) x (ny >> (levels-1-l)) cells, formed by merging
+ *   2x2 cells (Sec. 3.2.2).
+ * Cell state (Sec. 2.2, eq. truncated-dis, Grad choice): a parameter row
+ *   (u1, u2, u3, theta) and the coefficients f_alpha, |alpha| <= M, in graded
+ *   order (|alpha| ascending, then alpha_1 descending, then alpha_2
+ *   descending), N_M = (M+1)(M+2)(M+3)/6 doubles.  States handed to the
+ *   library must be in Grad form (f_0 = rho > 0, f_{e_d} = 0,
+ *   sum_d f_{2e_d} = 0, theta > 0), planar (u3 = 0 and f_alpha = 0 for odd
+ *   alpha_3: the symmetry of a flow with d/dx3 = 0).
+ * Device arrays are row-major: params [cells][4], coefficients
+ *   [cells][N_M] (dense, no padding), all FP64.
+ * Walls: index 0 bottom (y = 0), 1 right (x = lx), 2 top (y = ly),
+ *   3 left (x = 0).  A wall may move tangentially only.
+ *
+ * Memory and streams: the caller owns every device buffer, including the
+ * workspace handed to nrmg_create (size from nrmg_workspace_bytes); the
+ * library never allocates device memory and never frees caller memory.  All
+ * work is issued on the caller's stream (a cudaStream_t passed as void*).
+ * Calls that return host scalars synchronize that stream; the others are
+ * asynchronous.  Device-side failures (a non-physical state, a scheduler wait
+ * that ran out) are recorded in a device status word and returned by the next
+ * synchronizing call.  No call aborts or exits the process.  A context must
+ * be used from one host thread at a time.
+ */
+#ifndef NRMG_H
+#define NRMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NRMG_OK = 0,
+  NRMG_ERR_ARG = 1,           /* invalid argument; nothing was launched */
+  NRMG_ERR_CUDA = 2,          /* a CUDA call failed (launch or synchronize) */
+  NRMG_ERR_OOM = 3,           /* the workspace is smaller than nrmg_workspace_bytes */
+  NRMG_ERR_NONPHYSICAL = 4,   /* rho <= 0, theta <= 0 or a non-finite value appeared */
+  NRMG_ERR_NOT_CONVERGED = 5, /* nrmg_solve reached max_cycles above tol */
+  NRMG_ERR_TIMEOUT = 6        /* a sweep-scheduler wait ran out (about 2 s); results are invalid */
+} nrmg_status;
+
+typedef struct nrmg_ctx nrmg_ctx;
+
+/* nx, ny must be divisible by 2^(levels-1); 1 <= levels <= 16. */
+typedef struct {
+  int nx, ny;
+  double lx, ly;
+  int levels;
+} nrmg_grid;
+
+/* Wall velocity (u[n] = 0 along the wall normal, u[2] = 0), temperature and
+ * accommodation coefficient chi in [0,1] (1 = fully diffuse). */
+typedef struct {
+  double u[3];
+  double theta;
+  double chi;
+} nrmg_wall;
+
+typedef enum { NRMG_BGK = 0, NRMG_SHAKHOV = 1 } nrmg_model;
+
+/* Collision frequency nu = beta sqrt(pi/2) rho theta^(1-omega) / Kn
+ * (Sec. 4, eq. nu-shakhov); Pr is used by the Shakhov model
+ * (eq. Shakhov-f^E); Shakhov with Pr = 1 is BGK (Sec. 2.1). */
+typedef struct {
+  int model; /* nrmg_model */
+  double Pr, omega, beta;
+} nrmg_collision;
+
+/* Scheme and cycle options.
+ *   order 1: face states are cell states; order 2: linear reconstruction of
+ *     eq. (moments-recon) with slope 1 (central, as printed) or 2 (van Albada
+ *     limited); a cell next to a wall has zero slope along that axis.
+ *   cfl: CFL number of eq. (local-CFL) (the paper uses 0.9).
+ *   s1, s2: pre/post FS steps, s3: FS steps of the coarsest solver, gamma: 1
+ *     V-cycle, 2 W-cycle (Algorithm 2; the paper uses 2, 2, 4, 1).
+ *   precision: 0 = FP64 throughout (the only value accepted). */
+typedef struct {
+  int order, slope;
+  double cfl;
+  int s1, s2, s3, gamma;
+  int precision;
+} nrmg_opts;
+
+/* Bytes of device workspace nrmg_create needs; 0 when the arguments are invalid. */
+size_t nrmg_workspace_bytes(const nrmg_grid *grid, int M, const nrmg_opts *opts);
+
+/* Create a solver over a caller-owned device workspace (>= 256-byte aligned,
+ * ws_bytes >= nrmg_workspace_bytes).  M in [3, 16] (Shakhov's f^E needs
+ * |alpha| = 3 and conservation of energy by the flux needs M >= 3).  The
+ * initial state on every level is the global Maxwellian rho = 1, u = 0,
+ * theta = 1.  stream: cudaStream_t (NULL = legacy default stream).
+ * Errors: NRMG_ERR_ARG (bad sizes, M, Kn <= 0, theta_w <= 0, wall moving
+ * along its normal, unknown model/options), NRMG_ERR_OOM, NRMG_ERR_CUDA. */
+nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall walls[4],
+                        const nrmg_collision *coll, const nrmg_opts *opts, void *dev_workspace,
+                        size_t ws_bytes, void *cuda_stream, nrmg_ctx **out);
+
+/* Release the host-side context (the workspace stays with the caller). */
+nrmg_status nrmg_destroy(nrmg_ctx *ctx);
+
+/* Copy a state (device arrays, layout above) into level `level`.  Setting
+ * the finest level also resets the reference mass of the mass correction and
+ * the reference residual ||R(f^0)|| of eq. (relative-residual). */
+nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *dev_params, const double *dev_coeffs);
+
+/* Copy level `level`'s state out to device arrays (either may be NULL). */
+nrmg_status nrmg_get_state(nrmg_ctx *ctx, int level, double *dev_params, double *dev_coeffs);
+
+/* Set the right-hand side r of level `level` (the r of Algorithm 1),
+ * expanded in the per-cell bases dev_rparams; NULL pointers clear it (r = 0).
+ * Algorithm 2 overwrites the r of every level below the finest. */
+nrmg_status nrmg_set_rhs(nrmg_ctx *ctx, int level, const double *dev_rparams, const double *dev_rcoeffs);
+
+/* `steps` fast-sweeping steps FS(f, r) (Sec. 3.1, Algorithm 1) on level
+ * `level`, in place.  Each step runs the four sweeps D1..D4; every sweep
+ * reproduces the serial cell order of the paper exactly (anti-diagonal
+ * wavefronts with per-cell dependency counters).  Asynchronous. */
+nrmg_status nrmg_smooth(nrmg_ctx *ctx, int level, int steps);
+
+/* R_ij(f) - r_ij of every cell of level `level` (eq. ode-system, each row in
+ * its cell's basis) into dev_R_out ([cells][N_M], may be NULL), and the
+ * residual norm of eq. (relative-residual) into *norm_out (may be NULL;
+ * synchronizes when non-NULL). */
+nrmg_status nrmg_residual(nrmg_ctx *ctx, int level, double *dev_R_out, double *norm_out);
+
+/* One NMG_K(f, 0) step (Algorithm 2, gamma-cycle with s1/s2/s3 FS steps,
+ * restriction of eq. fH, coarse problem of eq. coarse-grid-problem, update of
+ * eq. rewritten-update), then the total-mass correction of the finest level.
+ * *rel_res_out (may be NULL) receives ||R(f)|| / ||R(f^0)||; synchronizes. */
+nrmg_status nrmg_fas_cycle(nrmg_ctx *ctx, double *rel_res_out);
+
+/* Cycles until ||R(f)|| / ||R(f^0)|| <= tol (eq. relative-residual) or
+ * max_cycles.  NRMG_ERR_NOT_CONVERGED when tol was not reached. */
+nrmg_status nrmg_solve(nrmg_ctx *ctx, double tol, int max_cycles, int *cycles_out, double *rel_res_out);
+
+/* Macroscopic fields of the finest level (eq. moments-relation) into
+ * dev_out [cells][14]: rho, u1, u2, u3, theta, s11, s12, s13, s22, s23, s33,
+ * q1, q2, q3.  Asynchronous. */
+nrmg_status nrmg_fields(nrmg_ctx *ctx, double *dev_out);
+
+/* Two-grid building blocks of Algorithm 2, for tests and custom cycles:
+ * setup computes the defect of level lf, restricts state and defect to level
+ * lf-1 and forms its r (eq. coarse-grid-problem); update applies
+ * eq. (rewritten-update) to level lf. */
+nrmg_status nrmg_two_grid_setup(nrmg_ctx *ctx, int lf);
+nrmg_status nrmg_two_grid_update(nrmg_ctx *ctx, int lf);
+
+/* Rescale the finest level to its reference total mass (the correction
+ * applied after each NMG step). */
+nrmg_status nrmg_mass_correct(nrmg_ctx *ctx);
+
+/* Synchronize the stream and return (and clear) the device status. */
+nrmg_status nrmg_sync(nrmg_ctx *ctx);
+
+/* Number of the library's kernel launches issued so far on this context. */
+long long nrmg_launch_count(const nrmg_ctx *ctx);
+
+/* Event timing of the sweep kernel (measurement aid; the paper has no counterpart).  While
+ * profiling is on, every FS^steps launch is bracketed by CUDA events on the context's stream
+ * (at most 65536 launches are recorded).  nrmg_fs_profile synchronizes, returns the summed
+ * event time in ms, the number of timed launches, and the cell updates they performed
+ * without and with a right-hand side r (any pointer may be NULL), then resets the record. */
+nrmg_status nrmg_set_profiling(nrmg_ctx *ctx, int on);
+nrmg_status nrmg_fs_profile(nrmg_ctx *ctx, double *ms, long long *launches, long long *updates_no_r,
+                            long long *updates_r);
+
+/* Human-readable name of a status, and the last error message of a context
+ * (a static empty string when there is none; ctx may be NULL). */
+const char *nrmg_status_str(nrmg_status s);
+const char *nrmg_last_error(const nrmg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRMG_H */

@@ -1,0 +1,805 @@
+// Host side of the C ABI declared in include/nrmg.h: argument checks, index tables, the
+// layout of the caller's workspace, and the FAS cycle of Algorithm 2 issued as kernel launches
+// on the caller's stream.
+#include "nrmg.h"
+#include "nrmg_internal.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+using namespace nrmg;
+
+namespace {
+
+// ------------------------------------------------------------------ index tables
+struct Tables {
+  int M = 0, N = 0;
+  std::vector<int> al;           // [N][3]
+  std::vector<int32_t> i32;      // tslot[3N], tshak[N], iq[12], is[6]
+  std::vector<uint16_t> u16;     // tmem[3N], tprev[3N], tnext[3N], tal[3N], tdeg[N]
+  std::vector<double> fact;      // [N]
+  int idx_axis[2][kMaxM + 1];
+  int idx_e[3], idx_2e[3];
+};
+
+int nmom(int M) { return (M + 1) * (M + 2) * (M + 3) / 6; }
+
+void build_tables(int M, Tables &T) {
+  T.M = M;
+  T.N = nmom(M);
+  const int N = T.N;
+  T.al.resize(3 * N);
+  std::vector<int> cube((M + 1) * (M + 1) * (M + 1), -1);
+  auto cidx = [&](int a, int b, int c) -> int {
+    if (a < 0 || b < 0 || c < 0 || a + b + c > M) return -1;
+    return cube[(a * (M + 1) + b) * (M + 1) + c];
+  };
+  int k = 0;
+  for (int deg = 0; deg <= M; ++deg)
+    for (int a1 = deg; a1 >= 0; --a1)
+      for (int a2 = deg - a1; a2 >= 0; --a2) {
+        int a3 = deg - a1 - a2;
+        T.al[3 * k] = a1;
+        T.al[3 * k + 1] = a2;
+        T.al[3 * k + 2] = a3;
+        cube[(a1 * (M + 1) + a2) * (M + 1) + a3] = k++;
+      }
+  T.i32.assign(4 * N + 18, -1);
+  T.u16.assign(13 * N, 0xFFFF);
+  T.fact.resize(N);
+  for (int d = 0; d < 3; ++d) {
+    // index lines along d: all alpha sharing alpha with alpha_d = 0, stored by ascending alpha_d
+    std::vector<int> s0(N, -1);
+    int pos = 0;
+    for (int o = 0; o < N; ++o) {
+      const int *a = &T.al[3 * o];
+      if (a[d] != 0) continue;
+      for (int m = 0;; ++m) {
+        int t[3] = {a[0], a[1], a[2]};
+        t[d] = m;
+        int q = cidx(t[0], t[1], t[2]);
+        if (q < 0) break;
+        T.u16[d * N + pos] = (uint16_t)q;
+        s0[q] = pos++;
+      }
+    }
+    // outputs sorted by line position (alpha_d) descending: a warp runs equal-length loops
+    std::vector<int> ord(N);
+    for (int o = 0; o < N; ++o) ord[o] = o;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return T.al[3 * x + d] > T.al[3 * y + d]; });
+    for (int r = 0; r < N; ++r) {
+      int o = ord[r];
+      T.i32[d * N + r] = o | (s0[o] << 11) | (T.al[3 * o + d] << 22);
+    }
+    for (int o = 0; o < N; ++o) {
+      int t[3] = {T.al[3 * o], T.al[3 * o + 1], T.al[3 * o + 2]};
+      t[d] -= 1;
+      int pm = cidx(t[0], t[1], t[2]);
+      t[d] += 2;
+      int pp = cidx(t[0], t[1], t[2]);
+      T.u16[3 * N + d * N + o] = pm < 0 ? 0xFFFF : (uint16_t)pm;
+      T.u16[6 * N + d * N + o] = pp < 0 ? 0xFFFF : (uint16_t)pp;
+      T.u16[9 * N + d * N + o] = (uint16_t)T.al[3 * o + d];
+    }
+  }
+  for (int o = 0; o < N; ++o) {
+    const int *a = &T.al[3 * o];
+    T.u16[12 * N + o] = (uint16_t)(a[0] + a[1] + a[2]);
+    double f = 1.0;
+    for (int d = 0; d < 3; ++d)
+      for (int q = 2; q <= a[d]; ++q) f *= q;
+    T.fact[o] = f;
+    // Shakhov target: alpha = 3 e_i, or e_i + 2 e_d with d != i
+    int sh = -1;
+    for (int i = 0; i < 3; ++i) {
+      if (a[i] == 3 && a[0] + a[1] + a[2] == 3) sh = i;
+      for (int d = 0; d < 3; ++d)
+        if (d != i && a[i] == 1 && a[d] == 2 && a[0] + a[1] + a[2] == 3) sh = i;
+    }
+    T.i32[3 * N + o] = sh;
+  }
+  // heat-flux indices iq[i] = {3e_i, 2e_0+e_i, 2e_1+e_i, 2e_2+e_i} and sigma indices e_i+e_j
+  for (int i = 0; i < 3; ++i) {
+    int e3[3] = {0, 0, 0};
+    e3[i] = 3;
+    T.i32[4 * N + 4 * i] = cidx(e3[0], e3[1], e3[2]);
+    for (int d = 0; d < 3; ++d) {
+      int t[3] = {0, 0, 0};
+      t[d] += 2;
+      t[i] += 1;
+      T.i32[4 * N + 4 * i + 1 + d] = cidx(t[0], t[1], t[2]);
+    }
+  }
+  int q = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      int t[3] = {0, 0, 0};
+      t[i] += 1;
+      t[j] += 1;
+      T.i32[4 * N + 12 + q++] = cidx(t[0], t[1], t[2]);
+    }
+  for (int ax = 0; ax < 2; ++ax)
+    for (int m = 0; m <= kMaxM; ++m) {
+      int t[3] = {0, 0, 0};
+      t[ax] = m;
+      T.idx_axis[ax][m] = m <= M ? cidx(t[0], t[1], t[2]) : -1;
+    }
+  for (int d = 0; d < 3; ++d) {
+    int t[3] = {0, 0, 0};
+    t[d] = 1;
+    T.idx_e[d] = cidx(t[0], t[1], t[2]);
+    t[d] = 2;
+    T.idx_2e[d] = cidx(t[0], t[1], t[2]);
+  }
+}
+
+// Largest root of He_n: largest eigenvalue of the Jacobi matrix (zero diagonal, off-diagonal
+// sqrt(k)), by bisection on the Sturm sequence count.
+double hermite_largest_root(int n) {
+  if (n <= 1) return 0.0;
+  auto count_below = [&](double x) {  // number of eigenvalues < x
+    int cnt = 0;
+    double q = -x;
+    if (q < 0) ++cnt;
+    for (int k = 1; k < n; ++k) {
+      double qq = (q == 0.0) ? 1e-300 : q;
+      q = -x - k / qq;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  double lo = 0.0, hi = 2.0 * sqrt((double)n) + 1.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (count_below(mid) < n)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Half-range moments J^s_{k,m} = int_{s v > 0} v He_k(v) He_m(v) phi(v) dv, via the
+// linearization He_k He_m = sum_j C(k,j) C(m,j) j! He_{k+m-2j}, v He_n = He_{n+1} + n He_{n-1}
+// and int_0^inf He_n phi = He_{n-1}(0) phi(0) (n >= 1), 1/2 (n = 0).  Long double limits the
+// cancellation of the alternating sum.
+void halfrange_table(int K, int s, std::vector<double> &J) {
+  typedef long double ld;
+  const ld pi = 3.141592653589793238462643383279502884L;
+  std::vector<ld> he0(2 * K + 4, 0.0L), A(2 * K + 4, 0.0L);
+  he0[0] = 1.0L;
+  he0[1] = 0.0L;
+  for (int n = 1; n + 1 < (int)he0.size(); ++n) he0[n + 1] = -(ld)n * he0[n - 1];
+  A[0] = 0.5L;
+  for (int n = 1; n < (int)A.size(); ++n) A[n] = he0[n - 1] / sqrtl(2.0L * pi);
+  auto vint = [&](int n) -> ld { return A[n + 1] + (n >= 1 ? (ld)n * A[n - 1] : 0.0L); };  // int_0^inf v He_n phi
+  J.assign((K + 1) * (K + 1), 0.0);
+  for (int k = 0; k <= K; ++k)
+    for (int m = 0; m <= K; ++m) {
+      ld acc = 0.0L, ck = 1.0L, cm = 1.0L, jf = 1.0L;
+      for (int j = 0; j <= std::min(k, m); ++j) {
+        if (j > 0) {
+          ck = ck * (ld)(k - j + 1) / (ld)j;
+          cm = cm * (ld)(m - j + 1) / (ld)j;
+          jf *= (ld)j;
+        }
+        acc += ck * cm * jf * vint(k + m - 2 * j);
+      }
+      // J^- = (-1)^{k+m+1} J^+ (reflection v -> -v)
+      ld sg = ((k + m + 1) % 2 == 0) ? 1.0L : -1.0L;
+      J[k * (K + 1) + m] = (double)(s > 0 ? acc : sg * acc);
+    }
+}
+
+const int kWallAxis[4] = {1, 0, 1, 0};
+const int kWallSign[4] = {-1, +1, +1, -1};
+
+// Wall matrices of the half-range Maxwell flux: W[k][m] = theta^((k-m+1)/2)/k!
+// (J^s_{k,m} + (1-chi)(-1)^m J^{-s}_{k,m}); rho_w = sum_m R[m] a_{m e_n} with
+// R[m] = s sqrt(2 pi) theta^(-m/2) J^s_{0,m}; incoming Maxwellian In[k] = chi theta^((k+1)/2)/k! J^{-s}_{k,0}.
+void wall_tables(int M, const nrmg_wall *walls, std::vector<double> &W, std::vector<double> &R,
+                 std::vector<double> &In) {
+  const int K1 = M + 1;
+  W.assign(4 * K1 * K1, 0.0);
+  R.assign(4 * K1, 0.0);
+  In.assign(4 * K1, 0.0);
+  for (int w = 0; w < 4; ++w) {
+    int s = kWallSign[w];
+    double th = walls[w].theta, chi = walls[w].chi;
+    std::vector<double> Js, Jm;
+    halfrange_table(M, s, Js);
+    halfrange_table(M, -s, Jm);
+    double kf = 1.0;
+    for (int k = 0; k <= M; ++k) {
+      if (k > 0) kf *= k;
+      for (int m = 0; m <= M; ++m) {
+        double sg = (m % 2 == 0) ? 1.0 : -1.0;
+        W[(w * K1 + k) * K1 + m] = pow(th, 0.5 * (k - m + 1)) / kf * (Js[k * K1 + m] + (1.0 - chi) * sg * Jm[k * K1 + m]);
+      }
+      In[w * K1 + k] = chi * pow(th, 0.5 * (k + 1)) / kf * Jm[k * K1 + 0];
+    }
+    for (int m = 0; m <= M; ++m) R[w * K1 + m] = s * sqrt(2.0 * M_PI) * pow(th, -0.5 * m) * Js[0 * K1 + m];
+  }
+}
+
+// ------------------------------------------------------------------ workspace layout
+struct Carver {
+  size_t off = 0;
+  char *base = nullptr;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? (T *)(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int pad4(int n) { return (n + 3) & ~3; }
+constexpr int kPartials = 8192;
+
+}  // namespace
+
+struct nrmg_ctx {
+  nrmg_grid grid;
+  int M, N, NP, levels;
+  double Kn;
+  nrmg_wall walls[4];
+  nrmg_collision coll;
+  nrmg_opts opts;
+  cudaStream_t stream;
+  int nsm;
+  int occ[4];
+  Consts K;
+  LevelDev lev[kMaxLev];
+  double *partials, *dscal;   // reduction scratch, device scalars
+  int *dstatus;
+  double *hpin;               // pinned host scalars
+  int *hpin_i;
+  double m0, res0;
+  int have_res0;
+  long long launches;
+  // event timing of FS launches
+  int profiling;
+  std::vector<cudaEvent_t> ev;
+  std::vector<long long> ev_upd;   // cell updates of each timed launch
+  std::vector<int> ev_hasr;
+  size_t ev_used;
+  char err[256];
+};
+
+namespace {
+
+void layout(const nrmg_grid *g, int M, Carver &cv, nrmg_ctx *ctx) {
+  const int N = nmom(M), NP = pad4(N);
+  // tables
+  int32_t *ti = cv.take<int32_t>(4 * N + 18);
+  uint16_t *tu = cv.take<uint16_t>(13 * N);
+  double *tf = cv.take<double>(N);
+  double *wW = cv.take<double>(4 * (M + 1) * (M + 1));
+  double *wR = cv.take<double>(4 * (M + 1));
+  double *wI = cv.take<double>(4 * (M + 1));
+  int *ctl = cv.take<int>(64);  // status, abort, queue
+  double *part = cv.take<double>(kPartials);
+  double *scal = cv.take<double>(64);
+  LevelDev lv[kMaxLev];
+  for (int l = g->levels - 1; l >= 0; --l) {
+    int sh = g->levels - 1 - l;
+    LevelDev &L = lv[l];
+    L.nx = g->nx >> sh;
+    L.ny = g->ny >> sh;
+    L.ncell = L.nx * L.ny;
+    L.dx = g->lx / L.nx;
+    L.dy = g->ly / L.ny;
+    size_t nc = L.ncell;
+    L.P = cv.take<double>(nc * 4);
+    L.F = cv.take<double>(nc * NP);
+    L.rP = cv.take<double>(nc * 4);
+    L.rF = cv.take<double>(nc * NP);
+    L.bP = cv.take<double>(nc * 4);
+    L.bF = cv.take<double>(nc * NP);
+    L.D = cv.take<double>(nc * NP);
+    L.ver = cv.take<int>(nc);
+    L.order = cv.take<int>(4 * nc);
+    L.has_r = 0;
+  }
+  if (ctx) {
+    ctx->K.tab_i32 = ti;
+    ctx->K.tab_u16 = tu;
+    ctx->K.tab_f64 = tf;
+    ctx->K.wallW = wW;
+    ctx->K.wallRho = wR;
+    ctx->K.wallIn = wI;
+    ctx->K.status = ctl;
+    ctx->K.abort_flag = ctl + 1;
+    ctx->K.queue = ctl + 2;
+    ctx->dstatus = ctl;
+    ctx->partials = part;
+    ctx->dscal = scal;
+    for (int l = 0; l < g->levels; ++l) ctx->lev[l] = lv[l];
+  }
+}
+
+bool grid_ok(const nrmg_grid *g) {
+  if (!g || g->levels < 1 || g->levels > kMaxLev || g->nx < 1 || g->ny < 1) return false;
+  if (!(g->lx > 0.0) || !(g->ly > 0.0)) return false;
+  int sh = g->levels - 1;
+  if ((g->nx >> sh) < 1 || (g->ny >> sh) < 1) return false;
+  if (((g->nx >> sh) << sh) != g->nx || ((g->ny >> sh) << sh) != g->ny) return false;
+  if ((long long)g->nx * g->ny > (1LL << 28)) return false;
+  return true;
+}
+
+bool opts_ok(const nrmg_opts *o) {
+  if (!o) return false;
+  if (o->order != 1 && o->order != 2) return false;
+  if (o->slope < 0 || o->slope > 2) return false;
+  if (!(o->cfl > 0.0) || o->s1 < 0 || o->s2 < 0 || o->s3 < 0 || o->gamma < 1 || o->gamma > 2) return false;
+  if (o->precision != 0) return false;
+  return true;
+}
+
+nrmg_status set_err(nrmg_ctx *c, nrmg_status s, const char *msg) {
+  if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
+  return s;
+}
+
+nrmg_status cuda_check(nrmg_ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return NRMG_OK;
+  if (c) snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
+  return NRMG_ERR_CUDA;
+}
+
+#define CK(expr)                                            \
+  do {                                                      \
+    nrmg_status _s = cuda_check(ctx, (expr), #expr);        \
+    if (_s != NRMG_OK) return _s;                           \
+  } while (0)
+
+int grid_for(nrmg_ctx *ctx, int which, long long work) {
+  long long g = (long long)ctx->nsm * std::max(1, ctx->occ[which]);
+  if (work < g) g = work;
+  if (g > kPartials) g = kPartials;
+  return (int)std::max(1LL, g);
+}
+
+// device status -> host, then clear it
+nrmg_status sync_status(nrmg_ctx *ctx) {
+  CK(cudaMemcpyAsync(ctx->hpin_i, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int st = ctx->hpin_i[0];
+  if (st != 0) {
+    CK(cudaMemsetAsync(ctx->dstatus, 0, 2 * sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    snprintf(ctx->err, sizeof(ctx->err), "device reported status %d", st);
+    return (nrmg_status)st;
+  }
+  return NRMG_OK;
+}
+
+nrmg_status smooth(nrmg_ctx *ctx, int level, int steps) {
+  if (steps <= 0) return NRMG_OK;
+  LevelDev &L = ctx->lev[level];
+  CK(cudaMemsetAsync(L.ver, 0, sizeof(int) * L.ncell, ctx->stream));
+  CK(cudaMemsetAsync(ctx->K.queue, 0, sizeof(int), ctx->stream));
+  int g = grid_for(ctx, 0, (long long)steps * 4 * L.ncell);
+  bool timed = ctx->profiling && ctx->ev_used + 2 <= ctx->ev.size();
+  if (timed) CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
+  CK(launch_fs(ctx->K, L, steps, g, ctx->stream));
+  if (timed) {
+    CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
+    ctx->ev_upd[ctx->ev_used / 2] = (long long)steps * 4 * L.ncell;
+    ctx->ev_hasr[ctx->ev_used / 2] = L.has_r;
+    ctx->ev_used += 2;
+  }
+  ctx->launches += 1;
+  return NRMG_OK;
+}
+
+// residual of a level: mode kResOut (R - r, dense stride out_stride, norm partials),
+// kResDefect, kResCoarseRhs
+nrmg_status residual(nrmg_ctx *ctx, int level, int mode, double *out, int out_stride, int *grid_out) {
+  LevelDev L = ctx->lev[level];
+  if (mode == kResCoarseRhs) L.has_r = 0;
+  int g = grid_for(ctx, 1, L.ncell);
+  CK(launch_residual(ctx->K, L, mode, out, out_stride, ctx->partials, g, ctx->stream));
+  ctx->launches += 1;
+  if (grid_out) *grid_out = g;
+  return NRMG_OK;
+}
+
+nrmg_status norm_of(nrmg_ctx *ctx, int level, double *out_dev_R, double *norm_host) {
+  int g = 0;
+  nrmg_status s = residual(ctx, level, kResOut, out_dev_R, ctx->N, &g);
+  if (s != NRMG_OK) return s;
+  CK(launch_reduce_norm(ctx->partials, g, 1.0 / (ctx->grid.lx * ctx->grid.ly), ctx->dscal, ctx->stream));
+  ctx->launches += 1;
+  if (norm_host) {
+    CK(cudaMemcpyAsync(ctx->hpin, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    nrmg_status st = sync_status(ctx);
+    if (st != NRMG_OK) return st;
+    *norm_host = ctx->hpin[0];
+  }
+  return NRMG_OK;
+}
+
+nrmg_status two_grid_setup(nrmg_ctx *ctx, int lf) {
+  nrmg_status s = residual(ctx, lf, kResDefect, nullptr, 0, nullptr);
+  if (s != NRMG_OK) return s;
+  int g = grid_for(ctx, 2, ctx->lev[lf - 1].ncell);
+  CK(launch_restrict(ctx->K, ctx->lev[lf], ctx->lev[lf - 1], g, ctx->stream));
+  ctx->launches += 1;
+  s = residual(ctx, lf - 1, kResCoarseRhs, nullptr, 0, nullptr);
+  if (s != NRMG_OK) return s;
+  ctx->lev[lf - 1].has_r = 1;
+  return NRMG_OK;
+}
+
+nrmg_status two_grid_update(nrmg_ctx *ctx, int lf) {
+  int g = grid_for(ctx, 3, ctx->lev[lf].ncell);
+  CK(launch_prolong(ctx->K, ctx->lev[lf], ctx->lev[lf - 1], g, ctx->stream));
+  ctx->launches += 1;
+  return NRMG_OK;
+}
+
+// Algorithm 2 on level k
+nrmg_status nmg(nrmg_ctx *ctx, int k) {
+  const nrmg_opts &o = ctx->opts;
+  nrmg_status s;
+  if (k == 0) return smooth(ctx, 0, o.s3);
+  if ((s = smooth(ctx, k, o.s1)) != NRMG_OK) return s;
+  if ((s = two_grid_setup(ctx, k)) != NRMG_OK) return s;
+  for (int g = 0; g < o.gamma; ++g)
+    if ((s = nmg(ctx, k - 1)) != NRMG_OK) return s;
+  if ((s = two_grid_update(ctx, k)) != NRMG_OK) return s;
+  return smooth(ctx, k, o.s2);
+}
+
+nrmg_status mass_correct(nrmg_ctx *ctx) {
+  LevelDev &L = ctx->lev[ctx->levels - 1];
+  int g = (int)std::min<long long>(std::max(1, (L.ncell + kThreads - 1) / kThreads), 1024);
+  CK(launch_mass(ctx->K, L, ctx->partials, g, ctx->dscal + 2, ctx->m0, true, ctx->stream));
+  ctx->launches += 3;
+  return NRMG_OK;
+}
+
+nrmg_status set_maxwellian(nrmg_ctx *ctx) {
+  int nmax = 0;
+  for (int l = 0; l < ctx->levels; ++l) nmax = std::max(nmax, ctx->lev[l].ncell);
+  std::vector<double> ones(nmax, 1.0);
+  for (int l = 0; l < ctx->levels; ++l) {
+    LevelDev &L = ctx->lev[l];
+    CK(cudaMemsetAsync(L.P, 0, sizeof(double) * 4 * L.ncell, ctx->stream));
+    CK(cudaMemsetAsync(L.F, 0, sizeof(double) * ctx->NP * L.ncell, ctx->stream));
+    CK(cudaMemsetAsync(L.rP, 0, sizeof(double) * 4 * L.ncell, ctx->stream));
+    CK(cudaMemsetAsync(L.rF, 0, sizeof(double) * ctx->NP * L.ncell, ctx->stream));
+    CK(cudaMemsetAsync(L.D, 0, sizeof(double) * ctx->NP * L.ncell, ctx->stream));
+    CK(cudaMemcpy2DAsync(L.F, sizeof(double) * ctx->NP, ones.data(), sizeof(double), sizeof(double), L.ncell,
+                         cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpy2DAsync(L.P + 3, sizeof(double) * 4, ones.data(), sizeof(double), sizeof(double), L.ncell,
+                         cudaMemcpyHostToDevice, ctx->stream));
+    L.has_r = 0;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->m0 = ctx->grid.lx * ctx->grid.ly;
+  ctx->have_res0 = 0;
+  return NRMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t nrmg_workspace_bytes(const nrmg_grid *grid, int M, const nrmg_opts *opts) {
+  if (!grid_ok(grid) || M < 3 || M > kMaxM || !opts_ok(opts)) return 0;
+  Carver cv;
+  layout(grid, M, cv, nullptr);
+  return cv.off + 256;
+}
+
+nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall walls[4],
+                        const nrmg_collision *coll, const nrmg_opts *opts, void *dev_workspace, size_t ws_bytes,
+                        void *cuda_stream, nrmg_ctx **out) {
+  if (!out) return NRMG_ERR_ARG;
+  *out = nullptr;
+  if (!grid_ok(grid) || M < 3 || M > kMaxM || !(Kn > 0.0) || !walls || !coll || !opts_ok(opts) || !dev_workspace)
+    return NRMG_ERR_ARG;
+  if (coll->model != NRMG_BGK && coll->model != NRMG_SHAKHOV) return NRMG_ERR_ARG;
+  if (!(coll->beta > 0.0) || !(coll->Pr > 0.0) || !isfinite(coll->omega)) return NRMG_ERR_ARG;
+  for (int w = 0; w < 4; ++w) {
+    if (!(walls[w].theta > 0.0) || walls[w].chi < 0.0 || walls[w].chi > 1.0) return NRMG_ERR_ARG;
+    if (walls[w].u[kWallAxis[w]] != 0.0 || walls[w].u[2] != 0.0) return NRMG_ERR_ARG;
+  }
+  if (((uintptr_t)dev_workspace & 255) != 0) return NRMG_ERR_ARG;
+  if (ws_bytes < nrmg_workspace_bytes(grid, M, opts)) return NRMG_ERR_OOM;
+
+  nrmg_ctx *ctx = new nrmg_ctx();
+  memset(ctx->err, 0, sizeof(ctx->err));
+  ctx->grid = *grid;
+  ctx->M = M;
+  ctx->N = nmom(M);
+  ctx->NP = pad4(ctx->N);
+  ctx->levels = grid->levels;
+  ctx->Kn = Kn;
+  memcpy(ctx->walls, walls, sizeof(nrmg_wall) * 4);
+  ctx->coll = *coll;
+  ctx->opts = *opts;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->launches = 0;
+  ctx->profiling = 0;
+  ctx->ev_used = 0;
+  Carver cv;
+  cv.base = (char *)dev_workspace;
+  layout(grid, M, cv, ctx);
+
+  int dev = 0;
+  nrmg_status s;
+  if ((s = cuda_check(ctx, cudaGetDevice(&dev), "cudaGetDevice")) != NRMG_OK) goto fail;
+  if ((s = cuda_check(ctx, cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev),
+                      "cudaDeviceGetAttribute")) != NRMG_OK)
+    goto fail;
+  if ((s = cuda_check(ctx, cudaMallocHost((void **)&ctx->hpin, 64 * sizeof(double)), "cudaMallocHost")) != NRMG_OK)
+    goto fail;
+  ctx->hpin_i = (int *)(ctx->hpin + 32);
+  {
+    Consts &K = ctx->K;
+    K.M = M;
+    K.N = ctx->N;
+    K.NP = ctx->NP;
+    K.reach = (opts->order == 2 && opts->slope != 0) ? 2 : 1;
+    K.slope = opts->order == 2 ? opts->slope : 0;
+    K.model = coll->model;
+    K.Kn = Kn;
+    K.Pr = coll->Pr;
+    K.omega = coll->omega;
+    K.beta = coll->beta;
+    K.cfl = opts->cfl;
+    K.C = hermite_largest_root(M + 1);
+    K.lx = grid->lx;
+    K.ly = grid->ly;
+    for (int w = 0; w < 4; ++w) {
+      for (int d = 0; d < 3; ++d) K.wall_u[w][d] = walls[w].u[d];
+      K.wall_theta[w] = walls[w].theta;
+    }
+    Tables T;
+    build_tables(M, T);
+    memcpy(K.idx_axis, T.idx_axis, sizeof(T.idx_axis));
+    memcpy(K.idx_e, T.idx_e, sizeof(T.idx_e));
+    memcpy(K.idx_2e, T.idx_2e, sizeof(T.idx_2e));
+    std::vector<double> W, R, In;
+    wall_tables(M, walls, W, R, In);
+    cudaStream_t st = ctx->stream;
+#define CKF(expr)                                                   \
+  if ((s = cuda_check(ctx, (expr), #expr)) != NRMG_OK) goto fail;
+    CKF(cudaMemcpyAsync((void *)K.tab_i32, T.i32.data(), T.i32.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync((void *)K.tab_u16, T.u16.data(), T.u16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync((void *)K.tab_f64, T.fact.data(), T.fact.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync((void *)K.wallW, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync((void *)K.wallRho, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync((void *)K.wallIn, In.data(), In.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemsetAsync(ctx->dstatus, 0, 64 * sizeof(int), st));
+    // sweep orders: cells of Dk by anti-diagonal, then by i
+    for (int l = 0; l < ctx->levels; ++l) {
+      LevelDev &L = ctx->lev[l];
+      std::vector<int> ord(4 * (size_t)L.ncell);
+      for (int k = 0; k < 4; ++k) {
+        int *o = ord.data() + (size_t)k * L.ncell;
+        int n = 0;
+        bool idesc = (k == 1 || k == 2), jdesc = (k == 2 || k == 3);
+        for (int dg = 0; dg <= L.nx + L.ny - 2; ++dg)
+          for (int a = 0; a < L.nx; ++a) {
+            int b = dg - a;
+            if (b < 0 || b >= L.ny) continue;
+            int i = idesc ? L.nx - 1 - a : a, j = jdesc ? L.ny - 1 - b : b;
+            o[n++] = j * L.nx + i;
+          }
+      }
+      CKF(cudaMemcpyAsync(L.order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+      CKF(cudaStreamSynchronize(st));
+    }
+    for (int w = 0; w < 4; ++w) ctx->occ[w] = occupancy_cell(M, ctx->NP, w);
+    if (ctx->occ[0] < 1) {
+      s = set_err(ctx, NRMG_ERR_ARG, "shared-memory footprint too large for this M");
+      goto fail;
+    }
+#undef CKF
+  }
+  if ((s = set_maxwellian(ctx)) != NRMG_OK) goto fail;
+  *out = ctx;
+  return NRMG_OK;
+fail:
+  if (ctx->hpin) cudaFreeHost(ctx->hpin);
+  delete ctx;
+  return s;
+}
+
+nrmg_status nrmg_destroy(nrmg_ctx *ctx) {
+  if (!ctx) return NRMG_ERR_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->hpin) cudaFreeHost(ctx->hpin);
+  delete ctx;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *P, const double *F) {
+  if (!ctx || level < 0 || level >= ctx->levels || !P || !F) return NRMG_ERR_ARG;
+  LevelDev &L = ctx->lev[level];
+  CK(cudaMemcpyAsync(L.P, P, sizeof(double) * 4 * L.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(launch_pack(F, ctx->N, L.F, ctx->NP, L.ncell, ctx->N, ctx->stream));
+  CK(launch_check_state(ctx->K, L.P, L.F, ctx->NP, L.ncell, ctx->stream));
+  ctx->launches += 2;
+  nrmg_status s = sync_status(ctx);
+  if (s != NRMG_OK) return set_err(ctx, s, "set_state: non-physical or non-finite state");
+  if (level == ctx->levels - 1) {
+    // reference mass of the correction
+    int g = (int)std::min<long long>(std::max(1, (L.ncell + kThreads - 1) / kThreads), 1024);
+    CK(launch_mass(ctx->K, L, ctx->partials, g, ctx->dscal + 2, 0.0, false, ctx->stream));
+    ctx->launches += 2;
+    CK(cudaMemcpyAsync(ctx->hpin, ctx->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->m0 = ctx->hpin[0];
+    ctx->have_res0 = 0;
+  }
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_get_state(nrmg_ctx *ctx, int level, double *P, double *F) {
+  if (!ctx || level < 0 || level >= ctx->levels) return NRMG_ERR_ARG;
+  LevelDev &L = ctx->lev[level];
+  if (P) CK(cudaMemcpyAsync(P, L.P, sizeof(double) * 4 * L.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (F) {
+    CK(launch_pack(L.F, ctx->NP, F, ctx->N, L.ncell, ctx->N, ctx->stream));
+    ctx->launches += 1;
+  }
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_set_rhs(nrmg_ctx *ctx, int level, const double *rP, const double *rF) {
+  if (!ctx || level < 0 || level >= ctx->levels) return NRMG_ERR_ARG;
+  LevelDev &L = ctx->lev[level];
+  if (!rP || !rF) {
+    L.has_r = 0;
+    return NRMG_OK;
+  }
+  CK(cudaMemcpyAsync(L.rP, rP, sizeof(double) * 4 * L.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(launch_pack(rF, ctx->N, L.rF, ctx->NP, L.ncell, ctx->N, ctx->stream));
+  ctx->launches += 1;
+  L.has_r = 1;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_smooth(nrmg_ctx *ctx, int level, int steps) {
+  if (!ctx || level < 0 || level >= ctx->levels || steps < 0) return NRMG_ERR_ARG;
+  return smooth(ctx, level, steps);
+}
+
+nrmg_status nrmg_residual(nrmg_ctx *ctx, int level, double *dev_R_out, double *norm_out) {
+  if (!ctx || level < 0 || level >= ctx->levels) return NRMG_ERR_ARG;
+  if (norm_out) return norm_of(ctx, level, dev_R_out, norm_out);
+  return residual(ctx, level, kResOut, dev_R_out, ctx->N, nullptr);
+}
+
+nrmg_status nrmg_fas_cycle(nrmg_ctx *ctx, double *rel_res_out) {
+  if (!ctx) return NRMG_ERR_ARG;
+  const int K = ctx->levels - 1;
+  nrmg_status s;
+  ctx->lev[K].has_r = 0;
+  if (!ctx->have_res0) {
+    if ((s = norm_of(ctx, K, nullptr, &ctx->res0)) != NRMG_OK) return s;
+    ctx->have_res0 = 1;
+  }
+  if ((s = nmg(ctx, K)) != NRMG_OK) return s;
+  if ((s = mass_correct(ctx)) != NRMG_OK) return s;
+  double r = 0.0;
+  if ((s = norm_of(ctx, K, nullptr, &r)) != NRMG_OK) return s;
+  if (rel_res_out) *rel_res_out = ctx->res0 > 0.0 ? r / ctx->res0 : 0.0;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_solve(nrmg_ctx *ctx, double tol, int max_cycles, int *cycles_out, double *rel_res_out) {
+  if (!ctx || !(tol >= 0.0) || max_cycles < 0) return NRMG_ERR_ARG;
+  const int K = ctx->levels - 1;
+  ctx->lev[K].has_r = 0;
+  nrmg_status s = norm_of(ctx, K, nullptr, &ctx->res0);
+  if (s != NRMG_OK) return s;
+  ctx->have_res0 = 1;
+  double rr = ctx->res0 > 0.0 ? 1.0 : 0.0;
+  int it = 0;
+  while (rr > tol && it < max_cycles) {
+    if ((s = nrmg_fas_cycle(ctx, &rr)) != NRMG_OK) break;
+    ++it;
+  }
+  if (cycles_out) *cycles_out = it;
+  if (rel_res_out) *rel_res_out = rr;
+  if (s == NRMG_OK && rr > tol) s = NRMG_ERR_NOT_CONVERGED;
+  return s;
+}
+
+nrmg_status nrmg_fields(nrmg_ctx *ctx, double *dev_out) {
+  if (!ctx || !dev_out) return NRMG_ERR_ARG;
+  CK(launch_fields(ctx->K, ctx->lev[ctx->levels - 1], dev_out, ctx->stream));
+  ctx->launches += 1;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_two_grid_setup(nrmg_ctx *ctx, int lf) {
+  if (!ctx || lf < 1 || lf >= ctx->levels) return NRMG_ERR_ARG;
+  return two_grid_setup(ctx, lf);
+}
+
+nrmg_status nrmg_two_grid_update(nrmg_ctx *ctx, int lf) {
+  if (!ctx || lf < 1 || lf >= ctx->levels) return NRMG_ERR_ARG;
+  return two_grid_update(ctx, lf);
+}
+
+nrmg_status nrmg_mass_correct(nrmg_ctx *ctx) {
+  if (!ctx) return NRMG_ERR_ARG;
+  return mass_correct(ctx);
+}
+
+nrmg_status nrmg_sync(nrmg_ctx *ctx) {
+  if (!ctx) return NRMG_ERR_ARG;
+  return sync_status(ctx);
+}
+
+long long nrmg_launch_count(const nrmg_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+nrmg_status nrmg_set_profiling(nrmg_ctx *ctx, int on) {
+  if (!ctx) return NRMG_ERR_ARG;
+  if (on && ctx->ev.empty()) {
+    const size_t n = 2 * 65536;
+    ctx->ev.resize(n);
+    for (size_t k = 0; k < n; ++k) CK(cudaEventCreate(&ctx->ev[k]));
+    ctx->ev_upd.assign(n / 2, 0);
+    ctx->ev_hasr.assign(n / 2, 0);
+  }
+  ctx->profiling = on ? 1 : 0;
+  ctx->ev_used = 0;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_fs_profile(nrmg_ctx *ctx, double *ms, long long *launches, long long *updates_no_r,
+                            long long *updates_r) {
+  if (!ctx) return NRMG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  double tot = 0.0;
+  long long u0 = 0, u1 = 0;
+  for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]));
+    tot += t;
+    if (ctx->ev_hasr[k / 2])
+      u1 += ctx->ev_upd[k / 2];
+    else
+      u0 += ctx->ev_upd[k / 2];
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = (long long)(ctx->ev_used / 2);
+  if (updates_no_r) *updates_no_r = u0;
+  if (updates_r) *updates_r = u1;
+  ctx->ev_used = 0;
+  return NRMG_OK;
+}
+
+const char *nrmg_status_str(nrmg_status s) {
+  switch (s) {
+    case NRMG_OK: return "NRMG_OK";
+    case NRMG_ERR_ARG: return "NRMG_ERR_ARG";
+    case NRMG_ERR_CUDA: return "NRMG_ERR_CUDA";
+    case NRMG_ERR_OOM: return "NRMG_ERR_OOM";
+    case NRMG_ERR_NONPHYSICAL: return "NRMG_ERR_NONPHYSICAL";
+    case NRMG_ERR_NOT_CONVERGED: return "NRMG_ERR_NOT_CONVERGED";
+    case NRMG_ERR_TIMEOUT: return "NRMG_ERR_TIMEOUT";
+  }
+  return "NRMG_UNKNOWN";
+}
+
+const char *nrmg_last_error(const nrmg_ctx *ctx) { return ctx ? ctx->err : ""; }
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Internal declarations shared by the host (C ABI) and device translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nrmg {
+
+constexpr int kMaxM = 16;
+constexpr int kMaxN = 969;   // C(19,3)
+constexpr int kMaxLev = 16;
+constexpr int kNV = 9;       // transform vectors per cell update: 4 faces x 2 sides + r
+constexpr int kThreads = 256;
+
+// Device status codes (same values as nrmg_status).
+constexpr int kStOk = 0, kStNonPhysical = 4, kStTimeout = 6;
+
+// Kernel modes of the Jacobi-style residual kernel.
+enum ResMode { kResOut = 0, kResDefect = 1, kResCoarseRhs = 2 };
+
+struct LevelDev {
+  int nx, ny, ncell;
+  double dx, dy;
+  double *P, *F;    // state: [ncell][4], [ncell][NP]
+  double *rP, *rF;  // right-hand side r and its expansion bases
+  double *bP, *bF;  // restricted state saved for the coarse-grid update
+  double *D;        // defect r - R(f)
+  int *ver;         // per-cell update counters of the sweep scheduler
+  int *order;       // [4][ncell]: cells of sweep Dk in anti-diagonal order
+  int has_r;
+};
+
+// Everything a kernel needs besides the level: scheme constants and
+// pointers to the index tables built by the host.
+struct Consts {
+  int M, N, NP;
+  int reach;   // stencil reach: 1 (first order) or 2 (second order)
+  int slope;   // 0 none, 1 central, 2 van Albada
+  int model;
+  double Kn, Pr, omega, beta, cfl, C;  // C = largest root of He_{M+1}
+  double lx, ly;
+  double wall_u[4][3], wall_theta[4];
+  // tables (global memory, copied to shared memory by each CTA)
+  const int *tab_i32;   // tslot[3][N], then tshak[N] (Shakhov target or -1)
+  const uint16_t *tab_u16;  // tmem[3][N], then tprev[3][N], tnext[3][N] (0xFFFF = none), tdeg[N]
+  const double *tab_f64;    // fact[N] (alpha!)
+  const double *wallW;      // [4][(M+1)^2]: W^s_{k,m}
+  const double *wallRho;    // [4][M+1]
+  const double *wallIn;     // [4][M+1]
+  int idx_axis[2][kMaxM + 1];  // index of m e_x, m e_y
+  int idx_e[3], idx_2e[3];
+  int *status;
+  int *abort_flag;
+  int *queue;
+};
+
+// Size in bytes of the dynamic shared memory of the cell kernels.
+size_t cell_smem_bytes(int M, int NP);
+
+// Launchers (device translation unit).  Each returns cudaGetLastError().
+cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, int grid, cudaStream_t st);
+cudaError_t launch_residual(const Consts &K, const LevelDev &L, int mode, double *out, int out_stride,
+                            double *partials, int grid, cudaStream_t st);
+cudaError_t launch_restrict(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st);
+cudaError_t launch_prolong(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st);
+cudaError_t launch_reduce_norm(const double *partials, int n, double scale, double *out, cudaStream_t st);
+// Total mass of level L into scal[0]; with apply, also scale every coefficient by m0 / mass
+// (scal[1]).
+cudaError_t launch_mass(const Consts &K, const LevelDev &L, double *partials, int grid, double *scal, double m0,
+                        bool apply, cudaStream_t st);
+cudaError_t launch_fields(const Consts &K, const LevelDev &L, double *out, cudaStream_t st);
+cudaError_t launch_pack(const double *src, int src_stride, double *dst, int dst_stride, int rows, int cols,
+                        cudaStream_t st);
+cudaError_t launch_check_state(const Consts &K, const double *P, const double *F, int stride, int ncell,
+                               cudaStream_t st);
+int occupancy_cell(int M, int NP, int which);  // CTAs per SM of kernel `which` (0 fs, 1 res, 2 restrict, 3 prolong)
+
+}  // namespace nrmg

@@ -1,0 +1,871 @@
+// Device code of the GB300 nonlinear-multigrid moment solver (Hu & Li, arXiv 2206.13164).
+//
+// One CTA of kThreads threads updates one cell at a time.  A cell update needs up to nine
+// re-expansions of a Hermite coefficient vector into another basis (Sec. 2.3); they are done
+// together as one batched transform in shared memory, three directional passes with one
+// output coefficient per thread, outputs ordered by the length of their index line so that the
+// 32 lanes of a warp run loops of equal length.  The path is FP64-ALU bound: a cell update
+// is tens of thousands of DFMAs against a few KB of state traffic.
+//
+// The Gauss-Seidel sweeps of Algorithm 1 run in one persistent launch per FS^s call.  CTAs take
+// (step, sweep, cell) items from a global counter in anti-diagonal order and wait, on per-cell
+// update counters, until every cell of the cross stencil holds exactly the version the serial
+// order of the paper would show it: the newest one for a neighbour that sweep Dk visits earlier,
+// the previous one otherwise.  This reproduces the serial sweep exactly while letting
+// consecutive sweeps and steps overlap.  Every wait has a time limit after which the kernel
+// records NRMG_ERR_TIMEOUT and all CTAs leave.
+#include "nrmg_internal.h"
+
+#include <math.h>
+
+namespace nrmg {
+
+#define VA_EPS2 1e-12  // van Albada smoothing constant (squared)
+
+// ------------------------------------------------------------------ shared-memory layout
+struct SLayout {
+  size_t st, VA, VB, vsrc, vdst, cf, sc, fact, ti32, vflag, iarr, tu16, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline SLayout make_layout(int M, int N, int NP) {
+  SLayout s;
+  size_t o = 0;
+  s.st = o;    o = al16(o + sizeof(double) * 9 * (4 + NP));
+  s.VA = o;    o = al16(o + sizeof(double) * kNV * NP);
+  s.VB = o;    o = al16(o + sizeof(double) * kNV * NP);
+  s.vsrc = o;  o = al16(o + sizeof(double) * kNV * 4);
+  s.vdst = o;  o = al16(o + sizeof(double) * kNV * 4);
+  s.cf = o;    o = al16(o + sizeof(double) * kNV * 3 * (M + 1));
+  s.sc = o;    o = al16(o + sizeof(double) * 64);
+  s.fact = o;  o = al16(o + sizeof(double) * N);
+  s.ti32 = o;  o = al16(o + sizeof(int) * 4 * N);
+  s.vflag = o; o = al16(o + sizeof(int) * kNV * 3);
+  s.iarr = o;  o = al16(o + sizeof(int) * 64);
+  s.tu16 = o;  o = al16(o + sizeof(uint16_t) * 13 * N);
+  s.total = o;
+  return s;
+}
+
+size_t cell_smem_bytes(int M, int NP) {
+  int N = (M + 1) * (M + 2) * (M + 3) / 6;
+  return make_layout(M, N, NP).total;
+}
+
+struct Sm {
+  double *st, *VA, *VB, *vsrc, *vdst, *cf, *sc, *fact;
+  int *tslot, *tshak, *vflag, *iarr;
+  uint16_t *tmem, *tprev, *tnext, *tal, *tdeg;
+};
+
+// iarr slots
+enum { I_ITEM = 0, I_NACT = 1, I_ACT = 2 /* ..2+kNV */, I_EX = 16 /* ..16+9 */, I_WALL = 28 /* ..28+4 */,
+       I_BAD = 34, I_ABORT = 35 };
+// sc slots
+enum { S_DT = 0, S_NU = 1, S_Q = 2 /* ..5 */, S_SLR = 8 /* ..16 */, S_RHOW = 16 /* ..20 */, S_NEWP = 24 /* ..28 */,
+       S_PH = 32 /* ..36 */, S_NORM = 40, S_RED = 44 /* ..44+8 warps */ };
+
+constexpr uint16_t kNone = 0xFFFF;
+
+__device__ inline Sm bind_smem(char *base, int M, int N, int NP) {
+  SLayout L = make_layout(M, N, NP);
+  Sm s;
+  s.st = (double *)(base + L.st);
+  s.VA = (double *)(base + L.VA);
+  s.VB = (double *)(base + L.VB);
+  s.vsrc = (double *)(base + L.vsrc);
+  s.vdst = (double *)(base + L.vdst);
+  s.cf = (double *)(base + L.cf);
+  s.sc = (double *)(base + L.sc);
+  s.fact = (double *)(base + L.fact);
+  s.tslot = (int *)(base + L.ti32);
+  s.tshak = s.tslot + 3 * N;
+  s.vflag = (int *)(base + L.vflag);
+  s.iarr = (int *)(base + L.iarr);
+  s.tmem = (uint16_t *)(base + L.tu16);
+  s.tprev = s.tmem + 3 * N;
+  s.tnext = s.tmem + 6 * N;
+  s.tal = s.tmem + 9 * N;
+  s.tdeg = s.tmem + 12 * N;
+  return s;
+}
+
+__device__ inline void load_tables(const Consts &K, Sm &s) {
+  const int N = K.N;
+  for (int e = threadIdx.x; e < 4 * N; e += kThreads) s.tslot[e] = K.tab_i32[e];
+  for (int e = threadIdx.x; e < 13 * N; e += kThreads) s.tmem[e] = K.tab_u16[e];
+  for (int e = threadIdx.x; e < N; e += kThreads) s.fact[e] = K.tab_f64[e];
+}
+
+// ------------------------------------------------------------------ memory-model helpers
+__device__ inline int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ inline unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ inline int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+__device__ inline void raise_status(const Consts &K, int code, bool abort_all) {
+  atomicCAS(K.status, 0, code);
+  if (abort_all) atomicExch(K.abort_flag, 1);
+}
+
+// ------------------------------------------------------------------ batched basis transform
+// Coefficients of exp(-a z - b z^2) = sum_k c_k z^k for every active vector and direction:
+// c_0 = 1, c_1 = -a, (k+1) c_{k+1} = -a c_k - 2 b c_{k-1}, with a = w~_d - w_d, b = (t~ - t)/2.
+// Flags: bit 0 the direction is the identity, bit 1 a = 0 (odd c_k vanish exactly).
+__device__ inline void setup_coeffs(const Consts &K, Sm &s) {
+  const int M = K.M, na = s.iarr[I_NACT];
+  for (int t = threadIdx.x; t < na * 3; t += kThreads) {
+    int v = s.iarr[I_ACT + t / 3], d = t % 3;
+    double a = s.vdst[v * 4 + d] - s.vsrc[v * 4 + d];
+    double b = 0.5 * (s.vdst[v * 4 + 3] - s.vsrc[v * 4 + 3]);
+    double *c = s.cf + (v * 3 + d) * (M + 1);
+    c[0] = 1.0;
+    c[1] = -a;
+    for (int k = 1; k < M; ++k) c[k + 1] = (-a * c[k] - 2.0 * b * c[k - 1]) / (k + 1);
+    s.vflag[v * 3 + d] = ((a == 0.0 && b == 0.0) ? 1 : 0) | (a == 0.0 ? 2 : 0);
+  }
+}
+
+// g = prod_d exp(-a_d S_d - b S_d^2) f for the active vectors: passes X->Y, Y->X, X->Y.
+// Output alpha of direction d sums c_k f_{alpha - k e_d}, k = 0..alpha_d; the index line of
+// alpha along d is stored contiguously in tmem (s0 = position of alpha itself).
+__device__ inline void transform_batch(const Consts &K, Sm &s, double *X, double *Y) {
+  const int N = K.N, NP = K.NP, M = K.M, na = s.iarr[I_NACT];
+  for (int d = 0; d < 3; ++d) {
+    const double *in = (d == 1) ? Y : X;
+    double *out = (d == 1) ? X : Y;
+    const int *slot = s.tslot + d * N;
+    const uint16_t *mem = s.tmem + d * N;
+    for (int q = threadIdx.x; q < na * N; q += kThreads) {
+      int vi = q / N, r = q - vi * N;
+      int v = s.iarr[I_ACT + vi];
+      int pk = slot[r];
+      int o = pk & 2047, s0 = (pk >> 11) & 2047, p = pk >> 22;
+      const double *x = in + v * NP;
+      int fl = s.vflag[v * 3 + d];
+      double acc = x[o];
+      if (!(fl & 1)) {
+        const double *c = s.cf + (v * 3 + d) * (M + 1);
+        if (fl & 2) {
+          for (int k = 2; k <= p; k += 2) acc = fma(c[k], x[mem[s0 - k]], acc);
+        } else {
+          for (int k = 1; k <= p; ++k) acc = fma(c[k], x[mem[s0 - k]], acc);
+        }
+      }
+      out[v * NP + o] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// rho, u, theta of g in a general basis p (eq. rho-u-theta with the moments of H_alpha).
+__device__ inline void macros(const Consts &K, const double *p, const double *g, double *out) {
+  double rho = g[0], f2 = 0.0, fe2 = 0.0, fe[3];
+  for (int d = 0; d < 3; ++d) {
+    fe[d] = g[K.idx_e[d]];
+    f2 += g[K.idx_2e[d]];
+    fe2 += fe[d] * fe[d];
+  }
+  out[0] = rho;
+  for (int d = 0; d < 3; ++d) out[1 + d] = p[d] + fe[d] / rho;
+  out[4] = p[3] + (2.0 * f2 - fe2 / rho) / (3.0 * rho);
+}
+
+__device__ inline double recon(int slope, double qm, double q0, double qp, bool on, int sd, double h) {
+  if (!on) return q0;
+  double g;
+  if (slope == 1) {
+    g = (qp - qm) / (2.0 * h);
+  } else {
+    double a = q0 - qm, b = qp - q0;
+    g = ((b * b + VA_EPS2) * a + (a * a + VA_EPS2) * b) / ((a * a + b * b + 2.0 * VA_EPS2) * h);
+  }
+  return q0 + sd * (0.5 * h) * g;
+}
+
+// stencil slots: 0 C, 1 E, 2 W, 3 N, 4 S, 5 EE, 6 WW, 7 NN, 8 SS
+__constant__ int c_nb_di[9] = {0, 1, -1, 0, 0, 2, -2, 0, 0};
+__constant__ int c_nb_dj[9] = {0, 0, 0, 1, -1, 0, 0, 2, -2};
+// face-state recipe of vector slot v = 2*face + side: stencil cell X, its lower and upper
+// neighbours along the face axis, and the side sd of X's face.
+__constant__ int c_fs_x[8] = {0, 1, 2, 0, 0, 3, 4, 0};
+__constant__ int c_fs_m[8] = {2, 0, 6, 2, 4, 0, 8, 4};
+__constant__ int c_fs_p[8] = {1, 5, 0, 1, 3, 7, 0, 3};
+__constant__ int c_fs_sd[8] = {1, -1, 1, -1, 1, -1, 1, -1};
+__constant__ int c_face_wall[4] = {1, 3, 2, 0};  // wall index behind face E, W, N, S
+__constant__ int c_face_nb[4] = {1, 2, 3, 4};    // stencil slot across face E, W, N, S
+__constant__ int c_wall_axis[4] = {1, 0, 1, 0};
+
+// ------------------------------------------------------------------ the cell operator
+// Loads the stencil of cell c (i,j) into shared memory and computes, per coefficient,
+// R_ij(f) - r_ij.  On return the threads own elements o = tid, tid + kThreads, ... of the
+// result through the callback `emit(o, R_o - r_o)`.  `coherent` selects L2-only loads (the
+// sweep kernel reads cells other CTAs have just written).
+template <bool kCoherent, typename Emit>
+__device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, int i, int j, Emit emit) {
+  const int N = K.N, NP = K.NP, tid = threadIdx.x;
+  const int c = j * L.nx + i;
+  // ---- stencil existence and the wall faces
+  if (tid < 9) {
+    int ii = i + c_nb_di[tid], jj = j + c_nb_dj[tid];
+    int reach = abs(c_nb_di[tid]) + abs(c_nb_dj[tid]);
+    s.iarr[I_EX + tid] = (ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && reach <= K.reach) ? 1 : 0;
+  }
+  __syncthreads();
+  // ---- load the stencil (params + coefficients)
+  for (int sl = 0; sl < 9; ++sl) {
+    if (!s.iarr[I_EX + sl]) continue;
+    int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
+    double *dst = s.st + sl * (4 + NP);
+    const double *srcP = L.P + (size_t)cc * 4, *srcF = L.F + (size_t)cc * NP;
+    for (int e = tid; e < 4 + N; e += kThreads) {
+      const double *ptr = e < 4 ? srcP + e : srcF + (e - 4);
+      dst[e] = kCoherent ? __ldcg(ptr) : *ptr;
+    }
+  }
+  if (tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
+  __syncthreads();
+  const double *pc = s.st;  // cell params, then coefficients at pc + 4
+  // ---- face states (eq. moments-recon) and the vectors to re-expand
+  for (int q = tid; q < 8 * (4 + N); q += kThreads) {
+    int v = q / (4 + N), e = q - v * (4 + N);
+    int f = v >> 1, side = v & 1;
+    bool wall = s.iarr[I_WALL + f];
+    if (wall && side) continue;
+    int ax = f >> 1;
+    int sx = c_fs_x[v], sm = c_fs_m[v], sp = c_fs_p[v];
+    bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + sm] && s.iarr[I_EX + sp];
+    double h = ax == 0 ? L.dx : L.dy;
+    double val = recon(K.slope, s.st[sm * (4 + NP) + e], s.st[sx * (4 + NP) + e], s.st[sp * (4 + NP) + e], on,
+                       c_fs_sd[v], h);
+    if (e < 4) {
+      s.vsrc[v * 4 + e] = val;
+      if (wall) {
+        int w = c_face_wall[f];
+        s.vdst[v * 4 + e] = e < 3 ? K.wall_u[w][e] : K.wall_theta[w];
+      } else {
+        s.vdst[v * 4 + e] = pc[e];
+      }
+    } else {
+      s.VA[v * NP + (e - 4)] = val;
+    }
+  }
+  if (L.has_r) {
+    for (int e = tid; e < 4 + N; e += kThreads) {
+      if (e < 4) {
+        s.vsrc[8 * 4 + e] = L.rP[(size_t)c * 4 + e];
+        s.vdst[8 * 4 + e] = pc[e];
+      } else {
+        s.VA[8 * NP + e - 4] = L.rF[(size_t)c * NP + e - 4];
+      }
+    }
+  }
+  if (tid == 0) {
+    int na = 0;
+    for (int f = 0; f < 4; ++f) {
+      s.iarr[I_ACT + na++] = 2 * f;
+      if (!s.iarr[I_WALL + f]) s.iarr[I_ACT + na++] = 2 * f + 1;
+    }
+    if (L.has_r) s.iarr[I_ACT + na++] = 8;
+    s.iarr[I_NACT] = na;
+  }
+  __syncthreads();
+  // ---- scalars: HLL speed bounds, collision frequency, Shakhov heat flux
+  if (tid < 4 && !s.iarr[I_WALL + tid]) {
+    int ax = tid >> 1;
+    const double *pm = s.vsrc + (2 * tid) * 4, *pp = s.vsrc + (2 * tid + 1) * 4;
+    s.sc[S_SLR + 2 * tid] = fmin(pm[ax] - K.C * sqrt(pm[3]), pp[ax] - K.C * sqrt(pp[3]));
+    s.sc[S_SLR + 2 * tid + 1] = fmax(pm[ax] + K.C * sqrt(pm[3]), pp[ax] + K.C * sqrt(pp[3]));
+  }
+  if (tid == 32) {
+    const double *f = pc + 4;
+    double rho = f[0], th = pc[3];
+    s.sc[S_NU] = K.beta * sqrt(M_PI / 2.0) * rho * pow(th, 1.0 - K.omega) / K.Kn;
+    double sq = sqrt(th);
+    s.sc[S_DT] = K.cfl / ((fabs(pc[0]) + K.C * sq) / L.dx + (fabs(pc[1]) + K.C * sq) / L.dy);
+  }
+  if (tid >= 64 && tid < 67 && K.model == 1) {
+    // q_i = 2 f_{3e_i} + sum_d f_{2e_d + e_i} (eq. moments-relation); indices are in tshak's tail
+    int ii = tid - 64;
+    const double *f = pc + 4;
+    const int *iq = K.tab_i32 + 4 * N + 4 * ii;  // idx(3e_i), idx(2e_0+e_i), idx(2e_1+e_i), idx(2e_2+e_i)
+    double q = 2.0 * f[iq[0]];
+    for (int d = 0; d < 3; ++d) q += f[iq[1 + d]];
+    s.sc[S_Q + ii] = q;
+  }
+  setup_coeffs(K, s);
+  __syncthreads();
+  // ---- batch A: face states -> cell basis, cell -> wall bases, r -> cell basis (result in VB)
+  transform_batch(K, s, s.VA, s.VB);
+  // ---- wall fluxes (half-range kinetic flux in the wall basis)
+  if (tid < 4 && s.iarr[I_WALL + tid]) {
+    int w = c_face_wall[tid], ax = c_wall_axis[w];
+    const double *a = s.VB + (2 * tid) * NP;
+    const double *wr = K.wallRho + w * (K.M + 1);
+    double rw = 0.0;
+    for (int m = 0; m <= K.M; ++m) rw += wr[m] * a[K.idx_axis[ax][m]];
+    s.sc[S_RHOW + tid] = rw;
+  }
+  __syncthreads();
+  {
+    int nw = 0, wf[4];
+    for (int f = 0; f < 4; ++f)
+      if (s.iarr[I_WALL + f]) wf[nw++] = f;
+    for (int q = tid; q < nw * N; q += kThreads) {
+      int k = q / N, r = q - k * N;
+      int f = wf[k], w = c_face_wall[f], ax = c_wall_axis[w];
+      int pk = s.tslot[ax * N + r];
+      int o = pk & 2047, s0 = (pk >> 11) & 2047, p = pk >> 22;
+      int b0 = s0 - p, deg = s.tdeg[o];
+      int Lm = K.M - (deg - p);
+      const double *a = s.VB + (2 * f) * NP;
+      const double *W = K.wallW + (size_t)w * (K.M + 1) * (K.M + 1) + p * (K.M + 1);
+      const uint16_t *mem = s.tmem + ax * N;
+      double g = 0.0;
+      for (int m = 0; m <= Lm; ++m) g = fma(a[mem[b0 + m]], W[m], g);
+      if (deg == p) g = fma(s.sc[S_RHOW + f], K.wallIn[w * (K.M + 1) + p], g);
+      s.VA[(2 * f) * NP + o] = g;
+    }
+    if (tid == 0) {
+      int na = 0;
+      for (int k = 0; k < nw; ++k) s.iarr[I_ACT + na++] = 2 * wf[k];
+      s.iarr[I_NACT] = na;
+    }
+    if (tid < 4 && s.iarr[I_WALL + tid]) {
+      int w = c_face_wall[tid];
+      double *src = s.vsrc + (2 * tid) * 4, *dst = s.vdst + (2 * tid) * 4;
+      for (int e = 0; e < 4; ++e) {
+        src[e] = e < 3 ? K.wall_u[w][e] : K.wall_theta[w];
+        dst[e] = pc[e];
+      }
+    }
+    __syncthreads();
+    if (nw > 0) {
+      setup_coeffs(K, s);
+      __syncthreads();
+      // ---- batch B: wall fluxes back into the cell basis (VA -> VB, wall slots only)
+      transform_batch(K, s, s.VA, s.VB);
+    }
+  }
+  // ---- assemble R = -(F_E - F_W)/dx - (F_N - F_S)/dy + Q (eq. ode-system)
+  const double *f = pc + 4;
+  const double nu = s.sc[S_NU];
+  for (int o = tid; o < N; o += kThreads) {
+    double Ff[4];
+#pragma unroll
+    for (int fc = 0; fc < 4; ++fc) {
+      if (s.iarr[I_WALL + fc]) {
+        Ff[fc] = s.VB[(2 * fc) * NP + o];
+      } else {
+        int ax = fc >> 1;
+        const double *am = s.VB + (2 * fc) * NP, *ap = s.VB + (2 * fc + 1) * NP;
+        uint16_t pr = s.tprev[ax * N + o], nx = s.tnext[ax * N + o];
+        double al1 = (double)(s.tal[ax * N + o] + 1);
+        double xm = pc[ax] * am[o], xp = pc[ax] * ap[o];
+        if (pr != kNone) {
+          xm += pc[3] * am[pr];
+          xp += pc[3] * ap[pr];
+        }
+        if (nx != kNone) {
+          xm += al1 * am[nx];
+          xp += al1 * ap[nx];
+        }
+        double sL = s.sc[S_SLR + 2 * fc], sR = s.sc[S_SLR + 2 * fc + 1];
+        if (sL >= 0.0)
+          Ff[fc] = xm;
+        else if (sR <= 0.0)
+          Ff[fc] = xp;
+        else
+          Ff[fc] = (sR * xm - sL * xp + sL * sR * (ap[o] - am[o])) / (sR - sL);
+      }
+    }
+    double fE = 0.0;
+    if (o == 0) {
+      fE = f[0];
+    } else if (K.model == 1) {
+      int t = s.tshak[o];
+      if (t >= 0) fE = (1.0 - K.Pr) * s.sc[S_Q + t] / 5.0;
+    }
+    double Q = nu * (fE - f[o]);
+    double R = -(Ff[0] - Ff[1]) / L.dx - (Ff[2] - Ff[3]) / L.dy + Q;
+    double r = L.has_r ? s.VB[8 * NP + o] : 0.0;
+    emit(o, R - r);
+  }
+}
+
+// Back to Grad form (Sec. 2.4): macroscopics of g (basis pc), project g into the new basis,
+// zero f_{e_d} and the round-off mean of f_{2e_d}.  g lives in VA slot 0; the result is left in
+// VB slot 0 and the new params in sc[S_NEWP..].  Returns true when the state is physical.
+__device__ inline bool regrad(const Consts &K, Sm &s, const double *pc) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double mac[5];
+    macros(K, pc, s.VA, mac);
+    for (int e = 0; e < 4; ++e) {
+      s.sc[S_NEWP + e] = mac[1 + e];
+      s.vsrc[e] = pc[e];
+      s.vdst[e] = mac[1 + e];
+    }
+    s.iarr[I_ACT] = 0;
+    s.iarr[I_NACT] = 1;
+    s.iarr[I_BAD] = !(isfinite(mac[0]) && isfinite(mac[4]) && mac[0] > 0.0 && mac[4] > 0.0);
+  }
+  __syncthreads();
+  setup_coeffs(K, s);
+  __syncthreads();
+  transform_batch(K, s, s.VA, s.VB);
+  if (tid == 0) {
+    double *g = s.VB;
+    for (int d = 0; d < 3; ++d) g[K.idx_e[d]] = 0.0;
+    double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) / 3.0;
+    for (int d = 0; d < 3; ++d) g[K.idx_2e[d]] -= s3;
+  }
+  __syncthreads();
+  int bad = 0;
+  for (int o = tid; o < K.N; o += kThreads) bad |= !isfinite(s.VB[o]);
+  bad = __syncthreads_or(bad);
+  return !(bad || s.iarr[I_BAD]);
+}
+
+__device__ inline double block_sum(double v, double *red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kThreads / 32; ++k) t += red[k];
+  return t;  // valid in thread 0
+}
+
+// ------------------------------------------------------------------ FS^steps (Algorithm 1)
+__global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int steps) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
+  load_tables(K, s);
+  __syncthreads();
+  const int tid = threadIdx.x, N = K.N, NP = K.NP;
+  const int ncell = L.ncell;
+  const long long total = (long long)steps * 4 * ncell;
+  for (;;) {
+    if (tid == 0) {
+      int it = atomicAdd(K.queue, 1);
+      if (ld_volatile(K.abort_flag)) it = (int)total;
+      s.iarr[I_ITEM] = it;
+    }
+    __syncthreads();
+    const long long item = s.iarr[I_ITEM];
+    if (item >= total) break;
+    const int st = (int)(item / (4LL * ncell));
+    const int k = (int)((item / ncell) % 4);
+    const int n = (int)(item % ncell);
+    const int c = L.order[(size_t)k * ncell + n];
+    const int i = c % L.nx, j = c / L.nx;
+    const int v = 4 * st + k + 1;  // the version this update produces
+    // ---- wait until the cross stencil holds the versions of the serial order
+    if (tid < 9) {
+      int di = c_nb_di[tid], dj = c_nb_dj[tid];
+      int ii = i + di, jj = j + dj;
+      int reach = abs(di) + abs(dj);
+      if (ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && reach <= K.reach) {
+        // sweep Dk: i ascending for D1, D4; j ascending for D1, D2 (outer loop i, inner j)
+        int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
+        bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
+        int need = (tid != 0 && before) ? v : v - 1;
+        const int *flag = L.ver + (size_t)jj * L.nx + ii;
+        if (ld_acquire(flag) < need) {
+          unsigned long long t0 = gtimer();
+          while (ld_acquire(flag) < need) {
+            if (ld_volatile(K.abort_flag)) break;
+            if (gtimer() - t0 > kWaitLimitNs) {
+              raise_status(K, kStTimeout, true);
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) s.iarr[I_ABORT] = ld_volatile(K.abort_flag);
+    __syncthreads();
+    if (s.iarr[I_ABORT]) break;
+    // ---- R_ij(f) - r_ij, then f + dt (R - r) into VA slot 0
+    cell_residual<true>(K, L, s, i, j, [&](int o, double Rr) { s.VA[o] = s.st[4 + o] + s.sc[S_DT] * Rr; });
+    __syncthreads();
+    // copy the cell's params (stencil slot 0 is overwritten by nothing below, but keep a copy)
+    double pcell[4];
+    for (int e = 0; e < 4; ++e) pcell[e] = s.st[e];
+    bool ok = regrad(K, s, pcell);
+    double *Fo = L.F + (size_t)c * NP;
+    for (int o = tid; o < N; o += kThreads) Fo[o] = s.VB[o];
+    if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+    if (!ok && tid == 0) raise_status(K, kStNonPhysical, true);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(L.ver + c, v);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ residual of every cell
+// mode kResOut: out[c*stride + o] = R - r and the weighted norm partials;
+// kResDefect: D = -(R - r); kResCoarseRhs: rF = R + rF (the level has no r during the call).
+__global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L, int mode, double *out,
+                                                            int out_stride, double *partials) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
+  load_tables(K, s);
+  __syncthreads();
+  const int tid = threadIdx.x, NP = K.NP;
+  double acc = 0.0;
+  for (int c = blockIdx.x; c < L.ncell; c += gridDim.x) {
+    const int i = c % L.nx, j = c / L.nx;
+    double loc = 0.0;
+    if (mode == kResOut) {
+      cell_residual<false>(K, L, s, i, j, [&](int o, double Rr) {
+        if (out) out[(size_t)c * out_stride + o] = Rr;
+        double th = s.st[3];
+        double w = s.fact[o] * pow(th, -(double)s.tdeg[o]);
+        loc += w * Rr * Rr;
+      });
+      double t = block_sum(loc, s.sc + S_RED);
+      if (tid == 0) acc += t * L.dx * L.dy;
+    } else if (mode == kResDefect) {
+      cell_residual<false>(K, L, s, i, j, [&](int o, double Rr) { L.D[(size_t)c * NP + o] = -Rr; });
+    } else {
+      cell_residual<false>(K, L, s, i, j,
+                           [&](int o, double Rr) { L.rF[(size_t)c * NP + o] = Rr + L.rF[(size_t)c * NP + o]; });
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && partials) partials[blockIdx.x] = acc;
+}
+
+// ------------------------------------------------------------------ restriction (Sec. 3.2.2)
+__global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev Lf, LevelDev Lc) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
+  load_tables(K, s);
+  __syncthreads();
+  const int tid = threadIdx.x, N = K.N, NP = K.NP;
+  for (int C = blockIdx.x; C < Lc.ncell; C += gridDim.x) {
+    const int I = C % Lc.nx, J = C / Lc.nx;
+    int fi[4] = {(2 * J) * Lf.nx + 2 * I, (2 * J) * Lf.nx + 2 * I + 1, (2 * J + 1) * Lf.nx + 2 * I,
+                 (2 * J + 1) * Lf.nx + 2 * I + 1};
+    // fine states into VA slots 0..3, fine defects into slots 4..7
+    for (int q = tid; q < 8 * N; q += kThreads) {
+      int v = q / N, o = q - v * N;
+      int cc = fi[v & 3];
+      s.VA[v * NP + o] = v < 4 ? Lf.F[(size_t)cc * NP + o] : Lf.D[(size_t)cc * NP + o];
+    }
+    if (tid < 32) {
+      int v = tid >> 2, e = tid & 3;
+      s.vsrc[v * 4 + e] = Lf.P[(size_t)fi[v & 3] * 4 + e];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // (u_H, theta_H) from conservation of mass, momentum and energy (eq. uH-thetaH-computation)
+      double rho = 0.0, mom[3] = {0.0, 0.0, 0.0}, en = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        const double *p = s.vsrc + q * 4;
+        double r = s.VA[q * NP];
+        rho += r;
+        for (int d = 0; d < 3; ++d) mom[d] += r * p[d];
+        en += r * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) + 3.0 * r * p[3];
+      }
+      rho *= 0.25;
+      for (int d = 0; d < 3; ++d) mom[d] *= 0.25;
+      en *= 0.25;
+      double *pH = s.sc + S_PH;
+      for (int d = 0; d < 3; ++d) pH[d] = mom[d] / rho;
+      pH[3] = (en - rho * (pH[0] * pH[0] + pH[1] * pH[1] + pH[2] * pH[2])) / (3.0 * rho);
+      for (int v = 0; v < 8; ++v) {
+        for (int e = 0; e < 4; ++e) s.vdst[v * 4 + e] = pH[e];
+        s.iarr[I_ACT + v] = v;
+      }
+      s.iarr[I_NACT] = 8;
+    }
+    __syncthreads();
+    setup_coeffs(K, s);
+    __syncthreads();
+    transform_batch(K, s, s.VA, s.VB);
+    // area means (eq. fH)
+    double *fH = s.VA, *RH = s.VA + NP;
+    for (int o = tid; o < N; o += kThreads) {
+      double a = 0.0, b = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        a += s.VB[q * NP + o];
+        b += s.VB[(4 + q) * NP + o];
+      }
+      fH[o] = a * 0.25;
+      RH[o] = b * 0.25;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int d = 0; d < 3; ++d) fH[K.idx_e[d]] = 0.0;
+      double s3 = (fH[K.idx_2e[0]] + fH[K.idx_2e[1]] + fH[K.idx_2e[2]]) / 3.0;
+      for (int d = 0; d < 3; ++d) fH[K.idx_2e[d]] -= s3;
+    }
+    __syncthreads();
+    for (int o = tid; o < N; o += kThreads) {
+      Lc.F[(size_t)C * NP + o] = fH[o];
+      Lc.bF[(size_t)C * NP + o] = fH[o];
+      Lc.rF[(size_t)C * NP + o] = RH[o];
+    }
+    if (tid < 4) {
+      double v = s.sc[S_PH + tid];
+      Lc.P[(size_t)C * 4 + tid] = v;
+      Lc.bP[(size_t)C * 4 + tid] = v;
+      Lc.rP[(size_t)C * 4 + tid] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ coarse-grid update (eq. rewritten-update)
+__global__ void __launch_bounds__(kThreads) prolong_kernel(Consts K, LevelDev Lf, LevelDev Lc) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
+  load_tables(K, s);
+  __syncthreads();
+  const int tid = threadIdx.x, N = K.N, NP = K.NP;
+  for (int c = blockIdx.x; c < Lf.ncell; c += gridDim.x) {
+    const int i = c % Lf.nx, j = c / Lf.nx;
+    const int C = (j / 2) * Lc.nx + i / 2;
+    // slot 1: restricted coarse state, slot 2: current coarse state, both into the fine basis
+    for (int q = tid; q < 2 * N; q += kThreads) {
+      int v = q / N, o = q - v * N;
+      s.VA[(1 + v) * NP + o] = v == 0 ? Lc.bF[(size_t)C * NP + o] : Lc.F[(size_t)C * NP + o];
+    }
+    if (tid < 8) {
+      int v = tid >> 2, e = tid & 3;
+      s.vsrc[(1 + v) * 4 + e] = v == 0 ? Lc.bP[(size_t)C * 4 + e] : Lc.P[(size_t)C * 4 + e];
+      s.vdst[(1 + v) * 4 + e] = Lf.P[(size_t)c * 4 + e];
+    }
+    if (tid < 4) s.sc[S_PH + tid] = Lf.P[(size_t)c * 4 + tid];
+    if (tid == 0) {
+      s.iarr[I_ACT] = 1;
+      s.iarr[I_ACT + 1] = 2;
+      s.iarr[I_NACT] = 2;
+    }
+    __syncthreads();
+    setup_coeffs(K, s);
+    __syncthreads();
+    transform_batch(K, s, s.VA, s.VB);
+    for (int o = tid; o < N; o += kThreads)
+      s.VA[o] = (Lf.F[(size_t)c * NP + o] - s.VB[1 * NP + o]) + s.VB[2 * NP + o];
+    __syncthreads();
+    double pcell[4];
+    for (int e = 0; e < 4; ++e) pcell[e] = s.sc[S_PH + e];
+    bool ok = regrad(K, s, pcell);
+    for (int o = tid; o < N; o += kThreads) Lf.F[(size_t)c * NP + o] = s.VB[o];
+    if (tid < 4) Lf.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+    if (!ok && tid == 0) raise_status(K, kStNonPhysical, false);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ reductions and small kernels
+__global__ void reduce_norm_kernel(const double *partials, int n, double scale, double *out) {
+  __shared__ double red[kThreads / 32];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += kThreads) v += partials[k];
+  double t = block_sum(v, red);
+  if (threadIdx.x == 0) out[0] = sqrt(t * scale);
+}
+
+__global__ void mass_partial_kernel(LevelDev L, int NP, double *partials) {
+  __shared__ double red[kThreads / 32];
+  double v = 0.0;
+  for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads)
+    v += L.F[(size_t)c * NP];
+  double t = block_sum(v, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// total mass sum_c rho_c * area into out[0]; the scale m0 / mass into out[1] when m0 > 0
+__global__ void mass_total_kernel(const double *partials, int n, double area, double m0, double *out) {
+  __shared__ double red[kThreads / 32];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += kThreads) v += partials[k];
+  double t = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    out[0] = t * area;
+    if (m0 > 0.0) out[1] = m0 / (t * area);
+  }
+}
+
+__global__ void mass_apply_kernel(LevelDev L, int NP, const double *scale) {
+  const double sc = scale[0];
+  size_t tot = (size_t)L.ncell * NP;
+  for (size_t q = (size_t)blockIdx.x * kThreads + threadIdx.x; q < tot; q += (size_t)gridDim.x * kThreads)
+    L.F[q] *= sc;
+}
+
+// Grad-basis fields (eq. moments-relation): rho, u, theta, sigma_ij = (1+delta_ij) f_{e_i+e_j},
+// q_i = 2 f_{3e_i} + sum_d f_{2e_d+e_i}.  The needed indices sit after the Shakhov table.
+__global__ void fields_kernel(Consts K, LevelDev L, double *out) {
+  for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads) {
+    const double *f = L.F + (size_t)c * K.NP, *p = L.P + (size_t)c * 4;
+    const int *iq = K.tab_i32 + 4 * K.N;       // [3][4] heat-flux indices
+    const int *is = K.tab_i32 + 4 * K.N + 12;  // [6] idx(e_i + e_j), i <= j
+    double *o = out + (size_t)c * 14;
+    o[0] = f[0];
+    for (int d = 0; d < 3; ++d) o[1 + d] = p[d];
+    o[4] = p[3];
+    int k = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b, ++k) o[5 + k] = (1.0 + (a == b)) * f[is[k]];
+    for (int a = 0; a < 3; ++a) {
+      double q = 2.0 * f[iq[4 * a]];
+      for (int d = 0; d < 3; ++d) q += f[iq[4 * a + 1 + d]];
+      o[11 + a] = q;
+    }
+  }
+}
+
+__global__ void pack_kernel(const double *src, int ss, double *dst, int ds, int rows, int cols) {
+  size_t tot = (size_t)rows * ds;
+  for (size_t q = (size_t)blockIdx.x * kThreads + threadIdx.x; q < tot; q += (size_t)gridDim.x * kThreads) {
+    size_t r = q / ds;
+    int col = (int)(q - r * ds);
+    dst[q] = col < cols ? src[r * ss + col] : 0.0;
+  }
+}
+
+// Admissibility of a state handed in through the C ABI: rho > 0, theta > 0, finite.
+__global__ void check_state_kernel(Consts K, const double *P, const double *F, int stride, int ncell) {
+  for (int c = blockIdx.x * kThreads + threadIdx.x; c < ncell; c += gridDim.x * kThreads) {
+    const double *p = P + (size_t)c * 4, *f = F + (size_t)c * stride;
+    bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(p[3]) && p[3] > 0.0 && f[0] > 0.0;
+    for (int o = 0; o < K.N && ok; ++o) ok = isfinite(f[o]);
+    if (!ok) atomicCAS(K.status, 0, kStNonPhysical);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static void init_attrs() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(fs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(restrict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(prolong_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  done = true;
+}
+template <typename Kern>
+static void ensure_smem_attr(Kern) {
+  init_attrs();
+}
+
+static size_t smem_for(const Consts &K) { return make_layout(K.M, K.N, K.NP).total; }
+
+cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, int grid, cudaStream_t st) {
+  ensure_smem_attr(fs_kernel);
+  fs_kernel<<<grid, kThreads, smem_for(K), st>>>(K, L, steps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Consts &K, const LevelDev &L, int mode, double *out, int out_stride,
+                            double *partials, int grid, cudaStream_t st) {
+  ensure_smem_attr(residual_kernel);
+  residual_kernel<<<grid, kThreads, smem_for(K), st>>>(K, L, mode, out, out_stride, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st) {
+  ensure_smem_attr(restrict_kernel);
+  restrict_kernel<<<grid, kThreads, smem_for(K), st>>>(K, Lf, Lc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st) {
+  ensure_smem_attr(prolong_kernel);
+  prolong_kernel<<<grid, kThreads, smem_for(K), st>>>(K, Lf, Lc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_norm(const double *partials, int n, double scale, double *out, cudaStream_t st) {
+  reduce_norm_kernel<<<1, kThreads, 0, st>>>(partials, n, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass(const Consts &K, const LevelDev &L, double *partials, int grid, double *scal, double m0,
+                        bool apply, cudaStream_t st) {
+  mass_partial_kernel<<<grid, kThreads, 0, st>>>(L, K.NP, partials);
+  mass_total_kernel<<<1, kThreads, 0, st>>>(partials, grid, L.dx * L.dy, m0, scal);
+  if (apply) {
+    int g2 = (int)(((size_t)L.ncell * K.NP + kThreads - 1) / kThreads);
+    if (g2 > 4096) g2 = 4096;
+    mass_apply_kernel<<<g2, kThreads, 0, st>>>(L, K.NP, scal + 1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const Consts &K, const LevelDev &L, double *out, cudaStream_t st) {
+  int g = (L.ncell + kThreads - 1) / kThreads;
+  if (g > 4096) g = 4096;
+  fields_kernel<<<g, kThreads, 0, st>>>(K, L, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const double *src, int src_stride, double *dst, int dst_stride, int rows, int cols,
+                        cudaStream_t st) {
+  size_t tot = (size_t)rows * dst_stride;
+  int g = (int)((tot + kThreads - 1) / kThreads);
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  pack_kernel<<<g, kThreads, 0, st>>>(src, src_stride, dst, dst_stride, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_state(const Consts &K, const double *P, const double *F, int stride, int ncell,
+                               cudaStream_t st) {
+  int g = (ncell + kThreads - 1) / kThreads;
+  if (g > 4096) g = 4096;
+  check_state_kernel<<<g, kThreads, 0, st>>>(K, P, F, stride, ncell);
+  return cudaGetLastError();
+}
+
+int occupancy_cell(int M, int NP, int which) {
+  int N = (M + 1) * (M + 2) * (M + 3) / 6;
+  size_t sm = make_layout(M, N, NP).total;
+  int nb = 0;
+  switch (which) {
+    case 0:
+      ensure_smem_attr(fs_kernel);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fs_kernel, kThreads, sm);
+      break;
+    case 1:
+      ensure_smem_attr(residual_kernel);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, residual_kernel, kThreads, sm);
+      break;
+    case 2:
+      ensure_smem_attr(restrict_kernel);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, restrict_kernel, kThreads, sm);
+      break;
+    default:
+      ensure_smem_attr(prolong_kernel);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, prolong_kernel, kThreads, sm);
+      break;
+  }
+  return nb;
+}
+
+}  // namespace nrmg

@@ -1,0 +1,268 @@
+"""Thin Python binding of the C ABI in ``include/nrmg.h`` (argument marshalling only).
+
+Every step of the solver runs in the CUDA kernels of ``libnrmg.so``; PyTorch provides the
+device memory (the workspace and the state/result tensors) and the stream.  There is no
+fallback: if the library is missing or CUDA is unavailable, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_longlong, c_size_t, c_void_p
+
+import torch
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONPHYSICAL, ERR_NOT_CONVERGED, ERR_TIMEOUT = range(7)
+BGK, SHAKHOV = 0, 1
+
+
+class NrmgError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {_status_name(status)} {detail}".strip())
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("lx", c_double), ("ly", c_double), ("levels", c_int)]
+
+
+class Wall(ctypes.Structure):
+    _fields_ = [("u", c_double * 3), ("theta", c_double), ("chi", c_double)]
+
+
+class Collision(ctypes.Structure):
+    _fields_ = [("model", c_int), ("Pr", c_double), ("omega", c_double), ("beta", c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("order", c_int), ("slope", c_int), ("cfl", c_double), ("s1", c_int), ("s2", c_int),
+                ("s3", c_int), ("gamma", c_int), ("precision", c_int)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libnrmg.so (building it first when the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libnrmg.so missing at {path}")
+        L = ctypes.CDLL(path)
+        L.nrmg_workspace_bytes.restype = c_size_t
+        L.nrmg_workspace_bytes.argtypes = [POINTER(Grid), c_int, POINTER(Opts)]
+        L.nrmg_create.restype = c_int
+        L.nrmg_create.argtypes = [POINTER(Grid), c_int, c_double, POINTER(Wall), POINTER(Collision), POINTER(Opts),
+                                  c_void_p, c_size_t, c_void_p, POINTER(c_void_p)]
+        L.nrmg_destroy.restype = c_int
+        L.nrmg_destroy.argtypes = [c_void_p]
+        for name in ("nrmg_set_state", "nrmg_get_state", "nrmg_set_rhs"):
+            getattr(L, name).restype = c_int
+            getattr(L, name).argtypes = [c_void_p, c_int, c_void_p, c_void_p]
+        L.nrmg_smooth.restype = c_int
+        L.nrmg_smooth.argtypes = [c_void_p, c_int, c_int]
+        L.nrmg_residual.restype = c_int
+        L.nrmg_residual.argtypes = [c_void_p, c_int, c_void_p, POINTER(c_double)]
+        L.nrmg_fas_cycle.restype = c_int
+        L.nrmg_fas_cycle.argtypes = [c_void_p, POINTER(c_double)]
+        L.nrmg_solve.restype = c_int
+        L.nrmg_solve.argtypes = [c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]
+        L.nrmg_fields.restype = c_int
+        L.nrmg_fields.argtypes = [c_void_p, c_void_p]
+        L.nrmg_two_grid_setup.restype = c_int
+        L.nrmg_two_grid_setup.argtypes = [c_void_p, c_int]
+        L.nrmg_two_grid_update.restype = c_int
+        L.nrmg_two_grid_update.argtypes = [c_void_p, c_int]
+        L.nrmg_mass_correct.restype = c_int
+        L.nrmg_mass_correct.argtypes = [c_void_p]
+        L.nrmg_sync.restype = c_int
+        L.nrmg_sync.argtypes = [c_void_p]
+        L.nrmg_launch_count.restype = c_longlong
+        L.nrmg_launch_count.argtypes = [c_void_p]
+        L.nrmg_set_profiling.restype = c_int
+        L.nrmg_set_profiling.argtypes = [c_void_p, c_int]
+        L.nrmg_fs_profile.restype = c_int
+        L.nrmg_fs_profile.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
+                                      POINTER(c_longlong)]
+        L.nrmg_peak_fma.restype = c_int
+        L.nrmg_peak_fma.argtypes = [c_int, c_int, c_void_p, POINTER(c_double)]
+        L.nrmg_status_str.restype = ctypes.c_char_p
+        L.nrmg_status_str.argtypes = [c_int]
+        L.nrmg_last_error.restype = ctypes.c_char_p
+        L.nrmg_last_error.argtypes = [c_void_p]
+        _lib = L
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().nrmg_status_str(s).decode()
+    except Exception:  # pragma: no cover - only while reporting another failure
+        return str(s)
+
+
+def nmom(M: int) -> int:
+    return (M + 1) * (M + 2) * (M + 3) // 6
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One cavity problem on the current CUDA device.
+
+    walls: four (u, theta, chi) triples in the order bottom, right, top, left.
+    Levels follow Algorithm 2: level 0 is the coarsest, ``levels-1`` the finest.
+    """
+
+    def __init__(self, nx, ny, M, Kn, walls, levels=1, lx=1.0, ly=1.0, model=BGK, Pr=2.0 / 3.0, omega=0.81,
+                 beta=1.0, order=1, slope=0, cfl=0.9, s1=2, s2=2, s3=4, gamma=1, precision=0, device=None,
+                 stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("nrmg needs a CUDA device")
+        self.L = lib()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.M, self.N, self.levels = M, nmom(M), levels
+        self.nx, self.ny = nx, ny
+        self.grid = Grid(nx, ny, lx, ly, levels)
+        self.opts = Opts(order, slope, cfl, s1, s2, s3, gamma, precision)
+        self.coll = Collision(model, Pr, omega, beta)
+        wa = (Wall * 4)()
+        for k, (u, th, chi) in enumerate(walls):
+            wa[k].u = (c_double * 3)(*u)
+            wa[k].theta = th
+            wa[k].chi = chi
+        self.walls = wa
+        nbytes = self.L.nrmg_workspace_bytes(ctypes.byref(self.grid), M, ctypes.byref(self.opts))
+        if nbytes == 0:
+            raise NrmgError(ERR_ARG, "nrmg_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = c_void_p()
+        st = self.L.nrmg_create(ctypes.byref(self.grid), M, Kn, wa, ctypes.byref(self.coll), ctypes.byref(self.opts),
+                                c_void_p(self.workspace.data_ptr()), nbytes, c_void_p(self.stream.cuda_stream),
+                                ctypes.byref(self.ctx))
+        if st != OK:
+            raise NrmgError(st, "nrmg_create")
+
+    # -- helpers
+    def _check(self, st, where):
+        if st != OK:
+            raise NrmgError(st, where, self.L.nrmg_last_error(self.ctx).decode())
+
+    def level_shape(self, level):
+        sh = self.levels - 1 - level
+        return self.ny >> sh, self.nx >> sh
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            self.L.nrmg_destroy(self.ctx)
+            self.ctx = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state
+    def set_state(self, params, coeffs, level=None):
+        level = self.levels - 1 if level is None else level
+        self._check(self.L.nrmg_set_state(self.ctx, level, _ptr(params), _ptr(coeffs)), "nrmg_set_state")
+
+    def get_state(self, level=None):
+        level = self.levels - 1 if level is None else level
+        ny, nx = self.level_shape(level)
+        P = torch.empty((ny * nx, 4), dtype=torch.float64, device=self.device)
+        F = torch.empty((ny * nx, self.N), dtype=torch.float64, device=self.device)
+        self._check(self.L.nrmg_get_state(self.ctx, level, _ptr(P), _ptr(F)), "nrmg_get_state")
+        return P, F
+
+    def set_rhs(self, level, rparams=None, rcoeffs=None):
+        self._check(self.L.nrmg_set_rhs(self.ctx, level, _ptr(rparams), _ptr(rcoeffs)), "nrmg_set_rhs")
+
+    # -- solver
+    def smooth(self, level, steps):
+        self._check(self.L.nrmg_smooth(self.ctx, level, steps), "nrmg_smooth")
+
+    def residual(self, level=None, want_R=True):
+        level = self.levels - 1 if level is None else level
+        ny, nx = self.level_shape(level)
+        R = torch.empty((ny * nx, self.N), dtype=torch.float64, device=self.device) if want_R else None
+        norm = c_double(0.0)
+        self._check(self.L.nrmg_residual(self.ctx, level, _ptr(R), ctypes.byref(norm)), "nrmg_residual")
+        return R, norm.value
+
+    def fas_cycle(self):
+        rel = c_double(0.0)
+        self._check(self.L.nrmg_fas_cycle(self.ctx, ctypes.byref(rel)), "nrmg_fas_cycle")
+        return rel.value
+
+    def solve(self, tol=1e-8, max_cycles=200, raise_on_fail=True):
+        cyc, rel = c_int(0), c_double(0.0)
+        st = self.L.nrmg_solve(self.ctx, tol, max_cycles, ctypes.byref(cyc), ctypes.byref(rel))
+        if raise_on_fail and st not in (OK, ERR_NOT_CONVERGED):
+            self._check(st, "nrmg_solve")
+        return st, cyc.value, rel.value
+
+    def fields(self):
+        out = torch.empty((self.ny * self.nx, 14), dtype=torch.float64, device=self.device)
+        self._check(self.L.nrmg_fields(self.ctx, _ptr(out)), "nrmg_fields")
+        return out.view(self.ny, self.nx, 14)
+
+    def two_grid_setup(self, lf):
+        self._check(self.L.nrmg_two_grid_setup(self.ctx, lf), "nrmg_two_grid_setup")
+
+    def two_grid_update(self, lf):
+        self._check(self.L.nrmg_two_grid_update(self.ctx, lf), "nrmg_two_grid_update")
+
+    def mass_correct(self):
+        self._check(self.L.nrmg_mass_correct(self.ctx), "nrmg_mass_correct")
+
+    def sync(self):
+        self._check(self.L.nrmg_sync(self.ctx), "nrmg_sync")
+
+    @property
+    def launches(self) -> int:
+        return int(self.L.nrmg_launch_count(self.ctx))
+
+    def set_profiling(self, on: bool):
+        self._check(self.L.nrmg_set_profiling(self.ctx, 1 if on else 0), "nrmg_set_profiling")
+
+    def fs_profile(self):
+        """(ms, launches, cell updates without r, cell updates with r) of the timed FS launches."""
+        ms, n, u0, u1 = c_double(0.0), c_longlong(0), c_longlong(0), c_longlong(0)
+        self._check(self.L.nrmg_fs_profile(self.ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(u0),
+                                           ctypes.byref(u1)), "nrmg_fs_profile")
+        return ms.value, n.value, u0.value, u1.value
+
+
+def peak_fma(precision: int = 0, iters: int = 4096, stream=None) -> float:
+    """Measured FMA rate (FLOP/s) of the current device: precision 0 FP64, 1 FP32."""
+    out = c_double(0.0)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().nrmg_peak_fma(precision, iters, c_void_p(s.cuda_stream), ctypes.byref(out))
+    if st != 0:
+        raise RuntimeError(f"nrmg_peak_fma failed ({st})")
+    return out.value
+
+
+def from_problem(prob, **kw) -> Solver:
+    """Build a Solver from any object with the fields of a cavity problem description."""
+    walls = [(tuple(w.u), w.theta, w.chi) for w in prob.walls]
+    return Solver(prob.nx, prob.ny, prob.M, prob.Kn, walls, levels=prob.levels, lx=prob.lx, ly=prob.ly,
+                  model=prob.model, Pr=prob.Pr, omega=prob.omega, beta=prob.beta, order=prob.order,
+                  slope=prob.slope, cfl=prob.cfl, s1=prob.s1, s2=prob.s2, s3=prob.s3, gamma=prob.gamma, **kw)

@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Tolerances: the kernels evaluate the same formulas as the oracle in FP64 with fused
+multiply-adds and a different summation order in reductions, so one residual evaluation or
+one FS step agrees to a few ulps of the largest entry (1e-12 relative is asserted); a
+converged solve agrees to 1e-10 relative per field (the bar for the plain FP64 path).
+"""
+import numpy as np
+import pytest
+
+import torch  # noqa: E402
+
+from conftest import oracle_solver  # noqa: E402
+from inputs import (BGK, SHAKHOV, heated_cavity, lid_cavity, random_rhs, random_state)  # noqa: E402
+from paper_2206_13164_gb300 import nrmg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def gpu(prob):
+    return nrmg.from_problem(prob, device=DEV)
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def N(t):
+    return t.detach().cpu().numpy()
+
+
+def assert_close(a, b, rel, what=""):
+    a, b = np.asarray(a), np.asarray(b)
+    scale = max(np.abs(b).max(), 1e-300)
+    err = np.abs(a - b).max() / scale
+    assert err <= rel, f"{what}: max rel err {err:.3e} > {rel:.1e}"
+
+
+def set_both(G, O, level, P, F):
+    G.set_state(T(P), T(F), level)
+    O.set_state(level, P, F)
+
+
+CASES = [
+    # (name, problem, random-state amplitude)
+    ("lid_o1_M3_13x7", lid_cavity(13, 3, 0.1, 0.3).replace(ny=7), 0.05),
+    ("lid_o1_M5_16", lid_cavity(16, 5, 0.1, 0.2), 0.05),
+    ("lid_o2c_M4_12x10", lid_cavity(12, 4, 0.2, 0.3, order=2, slope=1).replace(ny=10), 0.05),
+    ("lid_o2va_M6_16", lid_cavity(16, 6, 0.05, 0.5, order=2, slope=2), 0.05),
+    ("heat_shak_o2va_M5_16", heated_cavity(16, 5, 0.3, order=2, slope=2), 0.05),
+    ("lid_M8_o2va_10", lid_cavity(10, 8, 0.01, 0.5, order=2, slope=2), 0.03),
+    ("lid_M10_o2va_8", lid_cavity(8, 10, 0.01, 0.5, order=2, slope=2), 0.03),
+    ("partial_wall_chi", lid_cavity(9, 4, 0.1, 0.3, order=2, slope=2).replace(
+        walls=[w.__class__(u=w.u, theta=w.theta, chi=0.6) for w in lid_cavity(9, 4, 0.1, 0.3).walls]), 0.05),
+]
+
+
+@pytest.mark.parametrize("name,prob,amp", CASES, ids=[c[0] for c in CASES])
+def test_residual_parity(name, prob, amp):
+    rng = np.random.default_rng(100)
+    P, F = random_state(rng, prob.ny, prob.nx, prob.M, amp=amp)
+    G, O = gpu(prob), oracle_solver(prob)
+    set_both(G, O, 0, P, F)
+    Rg, ng = G.residual(0)
+    Ro, no = O.residual(0)
+    assert_close(N(Rg), Ro, 1e-12, "R")
+    assert abs(ng - no) <= 1e-12 * no
+
+
+@pytest.mark.parametrize("name,prob,amp", CASES, ids=[c[0] for c in CASES])
+def test_fs_step_parity(name, prob, amp):
+    rng = np.random.default_rng(101)
+    P, F = random_state(rng, prob.ny, prob.nx, prob.M, amp=amp)
+    G, O = gpu(prob), oracle_solver(prob)
+    set_both(G, O, 0, P, F)
+    G.smooth(0, 1)
+    O.smooth(0, 1)
+    Pg, Fg = G.get_state(0)
+    Po, Fo = O.get_state(0)
+    assert_close(N(Pg), Po, 1e-12, "params")
+    assert_close(N(Fg), Fo, 1e-12, "coeffs")
+
+
+def test_fs_parity_with_rhs_and_several_steps():
+    prob = lid_cavity(12, 5, 0.1, 0.3, order=2, slope=2)
+    rng = np.random.default_rng(102)
+    P, F = random_state(rng, 12, 12, 5)
+    rP, rF = random_rhs(rng, 12, 12, 5, amp=0.02)
+    G, O = gpu(prob), oracle_solver(prob)
+    set_both(G, O, 0, P, F)
+    G.set_rhs(0, T(rP), T(rF))
+    O.set_rhs(0, rP, rF)
+    G.smooth(0, 3)
+    O.smooth(0, 3)
+    Pg, Fg = G.get_state(0)
+    Po, Fo = O.get_state(0)
+    assert_close(N(Pg), Po, 1e-11, "params")
+    assert_close(N(Fg), Fo, 1e-11, "coeffs")
+    Rg, ng = G.residual(0)
+    Ro, no = O.residual(0)
+    assert_close(N(Rg), Ro, 1e-10, "R with r")
+
+
+def test_two_grid_transfer_parity():
+    prob = lid_cavity(24, 5, 0.1, 0.3, order=2, slope=2, levels=3).replace(ny=40)
+    rng = np.random.default_rng(103)
+    P, F = random_state(rng, 40, 24, 5)
+    G, O = gpu(prob), oracle_solver(prob)
+    set_both(G, O, 2, P, F)
+    G.two_grid_setup(2)
+    O.two_grid_setup(2)
+    Pg, Fg = G.get_state(1)
+    Po, Fo = O.get_state(1)
+    assert_close(N(Pg), Po, 1e-13, "restricted params")
+    assert_close(N(Fg), Fo, 1e-13, "restricted coeffs")
+    # the coarse problem's r: compare through a coarse smoothing step, which uses it
+    G.smooth(1, 1)
+    O.smooth(1, 1)
+    Pg, Fg = G.get_state(1)
+    Po, Fo = O.get_state(1)
+    assert_close(N(Fg), Fo, 1e-11, "coarse smoothed")
+    G.two_grid_update(2)
+    O.two_grid_update(2)
+    Pg, Fg = G.get_state(2)
+    Po, Fo = O.get_state(2)
+    assert_close(N(Pg), Po, 1e-11, "updated params")
+    assert_close(N(Fg), Fo, 1e-11, "updated coeffs")
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_fas_cycle_parity(gamma):
+    prob = lid_cavity(16, 4, 0.1, 0.3, order=2, slope=2, levels=2, gamma=gamma)
+    G, O = gpu(prob), oracle_solver(prob)
+    for _ in range(2):
+        rg = G.fas_cycle()
+        st, ro = O.fas_cycle()
+        assert abs(rg - ro) <= 1e-10 * ro
+    Pg, Fg = G.get_state()
+    Po, Fo = O.get_state()
+    assert_close(N(Pg), Po, 1e-11, "params")
+    assert_close(N(Fg), Fo, 1e-11, "coeffs")
+
+
+FIELDS = ["rho", "u1", "u2", "u3", "theta", "s11", "s12", "s13", "s22", "s23", "s33", "q1", "q2", "q3"]
+
+
+def compare_fields(fg, fo, rel=1e-10):
+    for k, name in enumerate(FIELDS):
+        a, b = fg[..., k], fo[..., k]
+        if np.abs(b).max() == 0.0:
+            assert np.abs(a).max() <= 1e-14, name
+        else:
+            assert_close(a, b, rel, name)
+
+
+def test_converged_solve_parity_lid_c1():
+    """Lid-driven cavity, BGK, Kn 0.1, lid 0.1, M=5, 32x32, first order, 3-level FAS (the small
+    cavity workload); both sides to relative residual 1e-8, fields to 1e-10."""
+    from inputs import config_c1
+
+    prob = config_c1()
+    G, O = gpu(prob), oracle_solver(prob)
+    sto, co, ro = O.solve(1e-8, 100)
+    stg, cg, rg = G.solve(1e-8, 100)
+    assert sto == 0 and stg == 0
+    assert cg == co
+    compare_fields(N(G.fields()), O.fields(), 1e-10)
+
+
+def test_converged_solve_parity_heated_second_order():
+    prob = heated_cavity(16, 5, 0.3, order=2, slope=2, levels=2)
+    G, O = gpu(prob), oracle_solver(prob)
+    sto, co, ro = O.solve(1e-8, 100)
+    stg, cg, rg = G.solve(1e-8, 100)
+    assert sto == 0 and stg == 0 and cg == co
+    fg = N(G.fields())
+    compare_fields(fg, O.fields(), 1e-10)
+    # mirror symmetry about x = 1/2: even rho, u_y, theta; odd u_x
+    for k, sign in ((0, 1), (2, 1), (4, 1), (1, -1)):
+        assert np.abs(fg[..., k] - sign * fg[:, ::-1, k]).max() <= 1e-7 * max(1.0, np.abs(fg[..., k]).max())
+
+
+def test_maxwellian_fixed_point_gpu():
+    prob = lid_cavity(16, 6, 0.1, 0.0, order=2, slope=2, levels=2, model=SHAKHOV)
+    G = gpu(prob)
+    for lev in (0, 1):
+        R, n = G.residual(lev)
+        assert n <= 1e-14 and N(R).max() <= 1e-14
+
+
+def test_mass_is_restored_after_each_cycle():
+    prob = lid_cavity(16, 4, 0.1, 0.4, order=2, slope=2, levels=2)
+    G = gpu(prob)
+    for _ in range(3):
+        G.fas_cycle()
+        rho = N(G.fields())[..., 0]
+        assert abs(rho.mean() - 1.0) < 1e-13
+
+
+def test_nonphysical_state_is_rejected():
+    prob = lid_cavity(8, 3, 0.1, 0.1)
+    G = gpu(prob)
+    P, F = random_state(np.random.default_rng(104), 8, 8, 3)
+    P[5, 3] = -1.0
+    with pytest.raises(nrmg.NrmgError) as e:
+        G.set_state(T(P), T(F))
+    assert e.value.status == nrmg.ERR_NONPHYSICAL
+    G.sync()  # the context stays usable
+
+
+@pytest.mark.parametrize("which", ["c2", "c3"])
+def test_full_size_residual_sampled(which):
+    """The full-size cavity workloads (256x256 M=10; 512x512 M=8 Shakhov), launched as the
+    benchmark launches them: residual of a random state at sampled cells against the oracle."""
+    from inputs import config_c2, config_c3
+
+    prob = config_c2() if which == "c2" else config_c3()
+    rng = np.random.default_rng(105)
+    P, F = random_state(rng, prob.ny, prob.nx, prob.M, amp=0.02)
+    G, O = gpu(prob), oracle_solver(prob)
+    top = prob.levels - 1
+    set_both(G, O, top, P, F)
+    Rg, _ = G.residual(top)
+    Rg = N(Rg)
+    cells = [(0, 0), (prob.nx - 1, prob.ny - 1), (1, prob.ny - 2), (prob.nx // 2, prob.ny // 2)]
+    cells += [tuple(x) for x in rng.integers(0, prob.nx, size=(12, 2))]
+    for i, j in cells:
+        ro = O.cell_residual(top, int(i), int(j))
+        assert_close(Rg[int(j) * prob.nx + int(i)], ro, 1e-12, f"cell {i},{j}")
