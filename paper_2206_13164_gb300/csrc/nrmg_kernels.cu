@@ -246,11 +246,17 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     bool wall = s.iarr[I_WALL + f];
     if (wall && side) continue;
     int ax = f >> 1;
-    int sx = c_fs_x[v], sm = c_fs_m[v], sp = c_fs_p[v];
-    bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + sm] && s.iarr[I_EX + sp];
-    double h = ax == 0 ? L.dx : L.dy;
-    double val = recon(K.slope, s.st[sm * (4 + NP) + e], s.st[sx * (4 + NP) + e], s.st[sp * (4 + NP) + e], on,
-                       c_fs_sd[v], h);
+    double val;
+    if (wall) {
+      // the cell is wall-adjacent along this axis: zero slope, its face state is its own state
+      val = s.st[e];
+    } else {
+      int sx = c_fs_x[v], sm = c_fs_m[v], sp = c_fs_p[v];
+      bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + sm] && s.iarr[I_EX + sp];
+      double h = ax == 0 ? L.dx : L.dy;
+      val = recon(K.slope, s.st[sm * (4 + NP) + e], s.st[sx * (4 + NP) + e], s.st[sp * (4 + NP) + e], on,
+                  c_fs_sd[v], h);
+    }
     if (e < 4) {
       s.vsrc[v * 4 + e] = val;
       if (wall) {
