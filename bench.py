@@ -9,7 +9,7 @@ van Albada reconstruction, 6 levels (coarsest 8x8), s1 = s2 = 2, s3 = 4.
 metric: cell-moment updates per second = 4 sweeps x cells x N_M per FS step, summed over the
 FS steps of every level in the timed cycles (residual evaluations are not counted).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload lid256|lid32|heat512]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload lid256|lid32|lid64|heat512]
 
 With --impl reference the CPU oracle (plain serial C) is timed on the host on a bounded sample
 of the same workload.  Multi-GPU runs (torchrun) solve one independent replica per GPU.
@@ -38,6 +38,9 @@ WORKLOADS = {
     "lid32": dict(nx=32, M=5, Kn=0.1, lid=0.1, heat=None, model=0, Pr=2 / 3, order=1, slope=0, levels=3,
                   desc="lid-driven cavity 32x32, M=5 (56 moments), BGK, Kn=0.1, lid 0.1, first order, "
                        "3-level FAS V-cycle (2,2,4)"),
+    "lid64": dict(nx=64, M=10, Kn=0.01, lid=0.5, heat=None, model=0, Pr=2 / 3, order=2, slope=2, levels=4,
+                  desc="lid-driven cavity 64x64, M=10 (286 moments), BGK, Kn=0.01, lid 0.5, "
+                       "2nd-order van Albada, 4-level FAS V-cycle (2,2,4) (small profiling case)"),
     "heat512": dict(nx=512, M=8, Kn=0.05, lid=0.0, heat=2.0, model=1, Pr=2 / 3, order=2, slope=2, levels=7,
                     desc="bottom-heated cavity 512x512, M=8 (165 moments), Shakhov Pr=2/3, Kn=0.05, "
                          "theta_bottom=2, 2nd-order van Albada, 7-level FAS V-cycle (2,2,4)"),
