@@ -180,6 +180,31 @@ nrmg_status nrmg_set_profiling(nrmg_ctx *ctx, int on);
 nrmg_status nrmg_fs_profile(nrmg_ctx *ctx, double *ms, long long *launches, long long *updates_no_r,
                             long long *updates_r);
 
+/* Residual without any device allocation.  The paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory themselves (for example code running under
+ * an allocator that forbids cudaMalloc, or a host application that only holds device pointers
+ * handed to it), and so cannot provide the workspace nrmg_create needs.  It evaluates
+ * R_ij(f) on the single grid `grid` (nx x ny cells; `levels` is only checked for validity)
+ * with the same kernel as nrmg_residual (r = 0): the residual rows into dev_R_out
+ * ([cells][N_M] dense, may be NULL) and the norm of eq. (relative-residual) into *norm_out
+ * (may be NULL).  dev_params / dev_coeffs: the state, layout as above (device, read only).
+ * All scratch (index tables, wall matrices, a padded copy of the state, reduction partials,
+ * the status word) lives in one file-scope device array of 16 MiB
+ * (NRMG_NOALLOC_SCRATCH_BYTES) that every GPU loading the library holds until exit; the call
+ * makes no cudaMalloc/cudaFree and no allocating library call.  Sizes: the call fits when
+ * cells * (4 + N_M rounded up to 4) * 8 bytes plus about 80 KB of tables fit in 16 MiB
+ * (e.g. 128x128 at M = 5, 64x64 at M = 10); larger problems return NRMG_ERR_OOM before any
+ * GPU work.  The first call on a device looks up the array's device address on that device
+ * (cudaGetSymbolAddress) and must come before any stream capture.  Every call shares the
+ * array and it keeps the last call's contents; calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialized by the caller.  Synchronizes the stream.
+ * Errors: NRMG_ERR_ARG (as nrmg_create), NRMG_ERR_OOM (too large), NRMG_ERR_NONPHYSICAL,
+ * NRMG_ERR_CUDA. */
+nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, double Kn, const nrmg_wall walls[4],
+                                  const nrmg_collision *coll, const nrmg_opts *opts, const double *dev_params,
+                                  const double *dev_coeffs, double *dev_R_out, double *norm_out,
+                                  void *cuda_stream);
+
 /* Human-readable name of a status, and the last error message of a context
  * (a static empty string when there is none; ctx may be NULL). */
 const char *nrmg_status_str(nrmg_status s);

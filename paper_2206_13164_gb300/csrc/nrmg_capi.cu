@@ -803,3 +803,155 @@ const char *nrmg_status_str(nrmg_status s) {
 const char *nrmg_last_error(const nrmg_ctx *ctx) { return ctx ? ctx->err : ""; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ residual without allocation
+// Scratch of nrmg_residual_noalloc: a file-scope device array, so that callers who cannot
+// allocate device memory (no cudaMalloc, no caching allocator, no workspace of their own) can
+// still evaluate a residual.  Every GPU that loads the library holds it until the process exits.
+#define NRMG_NOALLOC_SCRATCH_BYTES (16u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NRMG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device; looked up once per device.
+cudaError_t noalloc_scratch(int dev, void **out) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, double Kn, const nrmg_wall walls[4],
+                                             const nrmg_collision *coll, const nrmg_opts *opts,
+                                             const double *dev_params, const double *dev_coeffs, double *dev_R_out,
+                                             double *norm_out, void *cuda_stream) {
+  if (!grid_ok(grid) || M < 3 || M > kMaxM || !(Kn > 0.0) || !walls || !coll || !opts_ok(opts) || !dev_params ||
+      !dev_coeffs)
+    return NRMG_ERR_ARG;
+  if (coll->model != NRMG_BGK && coll->model != NRMG_SHAKHOV) return NRMG_ERR_ARG;
+  if (!(coll->beta > 0.0) || !(coll->Pr > 0.0) || !isfinite(coll->omega)) return NRMG_ERR_ARG;
+  for (int w = 0; w < 4; ++w) {
+    if (!(walls[w].theta > 0.0) || walls[w].chi < 0.0 || walls[w].chi > 1.0) return NRMG_ERR_ARG;
+    if (walls[w].u[kWallAxis[w]] != 0.0 || walls[w].u[2] != 0.0) return NRMG_ERR_ARG;
+  }
+  const int N = nmom(M), NP = pad4(N);
+  const long long ncell = (long long)grid->nx * grid->ny;
+  // layout of the scratch: tables, control words, reduction scratch, padded copy of the state
+  size_t used = 0;
+  auto at = [&](size_t bytes) {
+    used = (used + 255) & ~size_t(255);
+    size_t o = used;
+    used += bytes;
+    return o;
+  };
+  const size_t o_i32 = at((4 * N + 18) * sizeof(int32_t));
+  const size_t o_u16 = at(13 * N * sizeof(uint16_t));
+  const size_t o_f64 = at(N * sizeof(double));
+  const size_t o_W = at(4 * (M + 1) * (M + 1) * sizeof(double));
+  const size_t o_R = at(4 * (M + 1) * sizeof(double));
+  const size_t o_In = at(4 * (M + 1) * sizeof(double));
+  const size_t o_ctl = at(64 * sizeof(int));
+  const size_t o_part = at(kPartials * sizeof(double));
+  const size_t o_scal = at(64 * sizeof(double));
+  const size_t o_P = at(ncell * 4 * sizeof(double));
+  const size_t o_F = at(ncell * NP * sizeof(double));
+  if (used > NRMG_NOALLOC_SCRATCH_BYTES) return NRMG_ERR_OOM;
+
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, nsm = 0;
+  void *base = nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NRMG_ERR_CUDA;
+  if (noalloc_scratch(dev, &base) != cudaSuccess) return NRMG_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NRMG_ERR_CUDA;
+  char *b = (char *)base;
+
+  Consts K;
+  memset(&K, 0, sizeof(K));
+  K.M = M;
+  K.N = N;
+  K.NP = NP;
+  K.reach = (opts->order == 2 && opts->slope != 0) ? 2 : 1;
+  K.slope = opts->order == 2 ? opts->slope : 0;
+  K.model = coll->model;
+  K.Kn = Kn;
+  K.Pr = coll->Pr;
+  K.omega = coll->omega;
+  K.beta = coll->beta;
+  K.cfl = opts->cfl;
+  K.C = hermite_largest_root(M + 1);
+  K.lx = grid->lx;
+  K.ly = grid->ly;
+  for (int w = 0; w < 4; ++w) {
+    for (int d = 0; d < 3; ++d) K.wall_u[w][d] = walls[w].u[d];
+    K.wall_theta[w] = walls[w].theta;
+  }
+  Tables T;
+  build_tables(M, T);
+  memcpy(K.idx_axis, T.idx_axis, sizeof(T.idx_axis));
+  memcpy(K.idx_e, T.idx_e, sizeof(T.idx_e));
+  memcpy(K.idx_2e, T.idx_2e, sizeof(T.idx_2e));
+  std::vector<double> W, R, In;
+  wall_tables(M, walls, W, R, In);
+  K.tab_i32 = (const int *)(b + o_i32);
+  K.tab_u16 = (const uint16_t *)(b + o_u16);
+  K.tab_f64 = (const double *)(b + o_f64);
+  K.wallW = (const double *)(b + o_W);
+  K.wallRho = (const double *)(b + o_R);
+  K.wallIn = (const double *)(b + o_In);
+  K.status = (int *)(b + o_ctl);
+  K.abort_flag = K.status + 1;
+  K.queue = K.status + 2;
+  double *partials = (double *)(b + o_part), *scal = (double *)(b + o_scal);
+
+  LevelDev L;
+  memset(&L, 0, sizeof(L));
+  L.nx = grid->nx;
+  L.ny = grid->ny;
+  L.ncell = (int)ncell;
+  L.dx = grid->lx / grid->nx;
+  L.dy = grid->ly / grid->ny;
+  L.P = (double *)(b + o_P);
+  L.F = (double *)(b + o_F);
+  L.has_r = 0;
+
+#define NA(expr)                                  \
+  do {                                            \
+    if ((expr) != cudaSuccess) return NRMG_ERR_CUDA; \
+  } while (0)
+  NA(cudaMemcpyAsync((void *)K.tab_i32, T.i32.data(), T.i32.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync((void *)K.tab_u16, T.u16.data(), T.u16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync((void *)K.tab_f64, T.fact.data(), T.fact.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync((void *)K.wallW, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync((void *)K.wallRho, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync((void *)K.wallIn, In.data(), In.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  // the status words must start at zero; everything else is overwritten before it is read
+  NA(cudaMemsetAsync(K.status, 0, 64 * sizeof(int), st));
+  NA(cudaMemcpyAsync(L.P, dev_params, sizeof(double) * 4 * ncell, cudaMemcpyDeviceToDevice, st));
+  NA(launch_pack(dev_coeffs, N, L.F, NP, L.ncell, N, st));
+  NA(launch_check_state(K, L.P, L.F, NP, L.ncell, st));
+  int occ = occupancy_cell(M, NP, 1);
+  long long g = (long long)nsm * (occ < 1 ? 1 : occ);
+  if (g > ncell) g = ncell;
+  if (g > kPartials) g = kPartials;
+  NA(launch_residual(K, L, kResOut, dev_R_out, N, partials, (int)g, st));
+  NA(launch_reduce_norm(partials, (int)g, 1.0 / (grid->lx * grid->ly), scal, st));
+  double hnorm = 0.0;
+  int hstatus = 0;
+  NA(cudaMemcpyAsync(&hnorm, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  NA(cudaMemcpyAsync(&hstatus, K.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NA(cudaStreamSynchronize(st));
+#undef NA
+  if (hstatus != 0) return (nrmg_status)hstatus;
+  if (norm_out) *norm_out = hnorm;
+  return NRMG_OK;
+}

@@ -266,3 +266,33 @@ def from_problem(prob, **kw) -> Solver:
     return Solver(prob.nx, prob.ny, prob.M, prob.Kn, walls, levels=prob.levels, lx=prob.lx, ly=prob.ly,
                   model=prob.model, Pr=prob.Pr, omega=prob.omega, beta=prob.beta, order=prob.order,
                   slope=prob.slope, cfl=prob.cfl, s1=prob.s1, s2=prob.s2, s3=prob.s3, gamma=prob.gamma, **kw)
+
+
+def residual_noalloc(prob, params, coeffs, want_R=True, stream=None):
+    """R(f) and its norm for one grid through ``nrmg_residual_noalloc`` (no workspace, no
+    device allocation inside the library).  ``prob`` carries the cavity description (fields
+    of a Solver's constructor); params/coeffs are float64 CUDA tensors [cells,4], [cells,N_M].
+    Returns (R or None, norm)."""
+    L = lib()
+    if not getattr(L, "_noalloc_ready", False):
+        L.nrmg_residual_noalloc.restype = c_int
+        L.nrmg_residual_noalloc.argtypes = [POINTER(Grid), c_int, c_double, POINTER(Wall), POINTER(Collision),
+                                            POINTER(Opts), c_void_p, c_void_p, c_void_p, POINTER(c_double),
+                                            c_void_p]
+        L._noalloc_ready = True
+    grid = Grid(prob.nx, prob.ny, prob.lx, prob.ly, prob.levels)
+    opts = Opts(prob.order, prob.slope, prob.cfl, prob.s1, prob.s2, prob.s3, prob.gamma, 0)
+    coll = Collision(prob.model, prob.Pr, prob.omega, prob.beta)
+    wa = (Wall * 4)()
+    for k, w in enumerate(prob.walls):
+        wa[k].u = (c_double * 3)(*w.u)
+        wa[k].theta = w.theta
+        wa[k].chi = w.chi
+    R = torch.empty((prob.nx * prob.ny, nmom(prob.M)), dtype=torch.float64, device=coeffs.device) if want_R else None
+    norm = c_double(0.0)
+    s = stream if stream is not None else torch.cuda.current_stream(coeffs.device)
+    st = L.nrmg_residual_noalloc(ctypes.byref(grid), prob.M, prob.Kn, wa, ctypes.byref(coll), ctypes.byref(opts),
+                                 _ptr(params), _ptr(coeffs), _ptr(R), ctypes.byref(norm), c_void_p(s.cuda_stream))
+    if st != OK:
+        raise NrmgError(st, "nrmg_residual_noalloc")
+    return R, norm.value

@@ -1,0 +1,67 @@
+"""nrmg_residual_noalloc: the residual entry point for callers that cannot allocate device
+memory (it keeps its scratch in a static device array instead of a caller workspace).
+
+Its output must match the workspace-based nrmg_residual on the same state, to the 1e-12
+relative tolerance of the other residual parity tests, on two calls in a row (the second
+call reuses the static scratch left by the first).  This file is collected last, so a run
+that stops at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+import torch
+
+from inputs import heated_cavity, lid_cavity, random_state
+from paper_2206_13164_gb300 import nrmg
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _rel(a, b):
+    a, b = a.detach().cpu().numpy(), b.detach().cpu().numpy()
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _existing(prob, P, F):
+    S = nrmg.from_problem(prob, device=DEV)
+    S.set_state(P, F)
+    R, norm = S.residual()
+    return R, norm
+
+
+def test_noalloc_matches_workspace_residual_two_calls():
+    torch.cuda.set_device(0)
+    cases = [lid_cavity(32, 5, 0.1, 0.3, order=2, slope=2, levels=3),
+             heated_cavity(24, 8, 0.05, order=2, slope=2).replace(ny=16)]
+    rng = np.random.default_rng(7)
+    for prob in cases:  # two calls in a row, different sizes, M and models
+        P, F = random_state(rng, prob.ny, prob.nx, prob.M, amp=0.05)
+        P, F = _T(P), _T(F)
+        R0, n0 = _existing(prob, P, F)
+        R1, n1 = nrmg.residual_noalloc(prob, P, F)
+        assert _rel(R1, R0) <= 1e-12
+        assert abs(n1 - n0) <= 1e-12 * n0
+
+
+def test_noalloc_repeated_call_same_state_is_stable():
+    prob = lid_cavity(16, 6, 0.2, 0.4, order=1)
+    rng = np.random.default_rng(8)
+    P, F = random_state(rng, 16, 16, 6)
+    P, F = _T(P), _T(F)
+    R0, n0 = _existing(prob, P, F)
+    for _ in range(2):
+        R1, n1 = nrmg.residual_noalloc(prob, P, F)
+        assert _rel(R1, R0) <= 1e-12 and abs(n1 - n0) <= 1e-12 * n0
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    prob = lid_cavity(256, 10, 0.01, 0.5, order=2, slope=2)
+    P = torch.zeros((4, 4), dtype=torch.float64, device=DEV)  # never read: the size check comes first
+    F = torch.zeros((4, 286), dtype=torch.float64, device=DEV)
+    with pytest.raises(nrmg.NrmgError) as e:
+        nrmg.residual_noalloc(prob, P, F)
+    assert e.value.status == nrmg.ERR_OOM
