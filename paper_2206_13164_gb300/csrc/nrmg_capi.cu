@@ -296,6 +296,8 @@ void layout(const nrmg_grid *g, int M, Carver &cv, nrmg_ctx *ctx) {
     L.ncell = L.nx * L.ny;
     L.dx = g->lx / L.nx;
     L.dy = g->ly / L.ny;
+    L.idx = 1.0 / L.dx;
+    L.idy = 1.0 / L.dy;
     size_t nc = L.ncell;
     L.P = cv.take<double>(nc * 4);
     L.F = cv.take<double>(nc * NP);
@@ -920,6 +922,8 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   L.ncell = (int)ncell;
   L.dx = grid->lx / grid->nx;
   L.dy = grid->ly / grid->ny;
+  L.idx = 1.0 / L.dx;
+  L.idy = 1.0 / L.dy;
   L.P = (double *)(b + o_P);
   L.F = (double *)(b + o_F);
   L.has_r = 0;

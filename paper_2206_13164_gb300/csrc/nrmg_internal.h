@@ -20,6 +20,7 @@ enum ResMode { kResOut = 0, kResDefect = 1, kResCoarseRhs = 2 };
 struct LevelDev {
   int nx, ny, ncell;
   double dx, dy;
+  double idx, idy;  // 1/dx, 1/dy
   double *P, *F;    // state: [ncell][4], [ncell][NP]
   double *rP, *rF;  // right-hand side r and its expansion bases
   double *bP, *bF;  // restricted state saved for the coarse-grid update

@@ -23,22 +23,32 @@ namespace nrmg {
 #define VA_EPS2 1e-12  // van Albada smoothing constant (squared)
 
 // ------------------------------------------------------------------ shared-memory layout
+// cst: the cell's own state (params + coefficients).  VB doubles as the stencil buffer: the
+// eight neighbour states are only read while the face states are built, before the first
+// transform pass overwrites VB.
 struct SLayout {
-  size_t st, VA, VB, vsrc, vdst, cf, sc, fact, ti32, vflag, iarr, tu16, total;
+  size_t cst, VA, VB, vsrc, vdst, cf, sc, fact, ti32, vflag, iarr, tu16, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
+__host__ __device__ inline size_t vb_doubles(int NP) {
+  size_t a = (size_t)kNV * NP, b = (size_t)8 * (4 + NP);
+  return a > b ? a : b;
+}
+
+constexpr int kScal = 128;  // doubles of per-cell scalars
+
 __host__ __device__ inline SLayout make_layout(int M, int N, int NP) {
   SLayout s;
   size_t o = 0;
-  s.st = o;    o = al16(o + sizeof(double) * 9 * (4 + NP));
+  s.cst = o;   o = al16(o + sizeof(double) * (4 + NP));
   s.VA = o;    o = al16(o + sizeof(double) * kNV * NP);
-  s.VB = o;    o = al16(o + sizeof(double) * kNV * NP);
+  s.VB = o;    o = al16(o + sizeof(double) * vb_doubles(NP));
   s.vsrc = o;  o = al16(o + sizeof(double) * kNV * 4);
   s.vdst = o;  o = al16(o + sizeof(double) * kNV * 4);
   s.cf = o;    o = al16(o + sizeof(double) * kNV * 3 * (M + 1));
-  s.sc = o;    o = al16(o + sizeof(double) * 64);
+  s.sc = o;    o = al16(o + sizeof(double) * kScal);
   s.fact = o;  o = al16(o + sizeof(double) * N);
   s.ti32 = o;  o = al16(o + sizeof(int) * 4 * N);
   s.vflag = o; o = al16(o + sizeof(int) * kNV * 3);
@@ -54,7 +64,7 @@ size_t cell_smem_bytes(int M, int NP) {
 }
 
 struct Sm {
-  double *st, *VA, *VB, *vsrc, *vdst, *cf, *sc, *fact;
+  double *cst, *VA, *VB, *vsrc, *vdst, *cf, *sc, *fact;
   int *tslot, *tshak, *vflag, *iarr;
   uint16_t *tmem, *tprev, *tnext, *tal, *tdeg;
 };
@@ -63,15 +73,16 @@ struct Sm {
 enum { I_ITEM = 0, I_NACT = 1, I_ACT = 2 /* ..2+kNV */, I_EX = 16 /* ..16+9 */, I_WALL = 28 /* ..28+4 */,
        I_BAD = 34, I_ABORT = 35 };
 // sc slots
-enum { S_DT = 0, S_NU = 1, S_Q = 2 /* ..5 */, S_SLR = 8 /* ..16 */, S_RHOW = 16 /* ..20 */, S_NEWP = 24 /* ..28 */,
-       S_PH = 32 /* ..36 */, S_NORM = 40, S_RED = 44 /* ..44+8 warps */ };
+enum { S_DT = 0, S_NU = 1, S_Q = 2 /* ..5 */, S_W = 8 /* ..8+12: w1,w2,w3 per face */, S_RHOW = 20 /* ..24 */,
+       S_NEWP = 24 /* ..28 */, S_PH = 32 /* ..36 */, S_NORM = 40, S_RED = 44 /* ..44+8 warps */,
+       S_TPOW = 64 /* ..64+kMaxM+1: theta^-k */ };
 
 constexpr uint16_t kNone = 0xFFFF;
 
 __device__ inline Sm bind_smem(char *base, int M, int N, int NP) {
   SLayout L = make_layout(M, N, NP);
   Sm s;
-  s.st = (double *)(base + L.st);
+  s.cst = (double *)(base + L.cst);
   s.VA = (double *)(base + L.VA);
   s.VB = (double *)(base + L.VB);
   s.vsrc = (double *)(base + L.vsrc);
@@ -89,6 +100,11 @@ __device__ inline Sm bind_smem(char *base, int M, int N, int NP) {
   s.tal = s.tmem + 9 * N;
   s.tdeg = s.tmem + 12 * N;
   return s;
+}
+
+// state of stencil slot sl (0 = the cell, 1..8 = neighbours E, W, N, S, EE, WW, NN, SS)
+__device__ inline double *stencil(const Sm &s, int sl, int NP) {
+  return sl == 0 ? s.cst : s.VB + (size_t)(sl - 1) * (4 + NP);
 }
 
 __device__ inline void load_tables(const Consts &K, Sm &s) {
@@ -122,6 +138,11 @@ __device__ inline void raise_status(const Consts &K, int code, bool abort_all) {
 }
 
 // ------------------------------------------------------------------ batched basis transform
+// 1/(k+1), k = 0..kMaxM+1, so the coefficient recurrence needs no division
+__constant__ double c_inv[kMaxM + 2] = {1.0,       1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
+                                        1.0 / 7,   1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12,
+                                        1.0 / 13,  1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18};
+
 // Coefficients of exp(-a z - b z^2) = sum_k c_k z^k for every active vector and direction:
 // c_0 = 1, c_1 = -a, (k+1) c_{k+1} = -a c_k - 2 b c_{k-1}, with a = w~_d - w_d, b = (t~ - t)/2.
 // Flags: bit 0 the direction is the identity, bit 1 a = 0 (odd c_k vanish exactly).
@@ -134,7 +155,7 @@ __device__ inline void setup_coeffs(const Consts &K, Sm &s) {
     double *c = s.cf + (v * 3 + d) * (M + 1);
     c[0] = 1.0;
     c[1] = -a;
-    for (int k = 1; k < M; ++k) c[k + 1] = (-a * c[k] - 2.0 * b * c[k - 1]) / (k + 1);
+    for (int k = 1; k < M; ++k) c[k + 1] = (-a * c[k] - 2.0 * b * c[k - 1]) * c_inv[k];
     s.vflag[v * 3 + d] = ((a == 0.0 && b == 0.0) ? 1 : 0) | (a == 0.0 ? 2 : 0);
   }
 }
@@ -184,52 +205,48 @@ __device__ inline void macros(const Consts &K, const double *p, const double *g,
   out[4] = p[3] + (2.0 * f2 - fe2 / rho) / (3.0 * rho);
 }
 
-__device__ inline double recon(int slope, double qm, double q0, double qp, bool on, int sd, double h) {
-  if (!on) return q0;
-  double g;
-  if (slope == 1) {
-    g = (qp - qm) / (2.0 * h);
-  } else {
-    double a = q0 - qm, b = qp - q0;
-    g = ((b * b + VA_EPS2) * a + (a * a + VA_EPS2) * b) / ((a * a + b * b + 2.0 * VA_EPS2) * h);
-  }
-  return q0 + sd * (0.5 * h) * g;
+// Half of the limited slope times the cell width, q_face = q0 +- hs (eq. moments-recon with the
+// slope of the central difference, or of the van Albada average (b^2+e)a + (a^2+e)b over
+// a^2 + b^2 + 2e = (a+b)(ab+e) / (a^2+b^2+2e), a = q0 - qm, b = qp - q0).
+__device__ inline double half_slope(int slope, double qm, double q0, double qp) {
+  if (slope == 1) return 0.25 * (qp - qm);
+  double a = q0 - qm, b = qp - q0;
+  return 0.5 * ((a + b) * fma(a, b, VA_EPS2)) / fma(a, a, fma(b, b, 2.0 * VA_EPS2));
 }
 
 // stencil slots: 0 C, 1 E, 2 W, 3 N, 4 S, 5 EE, 6 WW, 7 NN, 8 SS
 __constant__ int c_nb_di[9] = {0, 1, -1, 0, 0, 2, -2, 0, 0};
 __constant__ int c_nb_dj[9] = {0, 0, 0, 1, -1, 0, 0, 2, -2};
-// face-state recipe of vector slot v = 2*face + side: stencil cell X, its lower and upper
-// neighbours along the face axis, and the side sd of X's face.
-__constant__ int c_fs_x[8] = {0, 1, 2, 0, 0, 3, 4, 0};
-__constant__ int c_fs_m[8] = {2, 0, 6, 2, 4, 0, 8, 4};
-__constant__ int c_fs_p[8] = {1, 5, 0, 1, 3, 7, 0, 3};
-__constant__ int c_fs_sd[8] = {1, -1, 1, -1, 1, -1, 1, -1};
+// slope items: cell X with its lower / upper neighbours along the item's axis
+__constant__ int c_it_x[6] = {0, 0, 1, 2, 3, 4};
+__constant__ int c_it_m[6] = {2, 4, 0, 6, 0, 8};
+__constant__ int c_it_p[6] = {1, 3, 5, 0, 7, 0};
 __constant__ int c_face_wall[4] = {1, 3, 2, 0};  // wall index behind face E, W, N, S
 __constant__ int c_face_nb[4] = {1, 2, 3, 4};    // stencil slot across face E, W, N, S
 __constant__ int c_wall_axis[4] = {1, 0, 1, 0};
 
 // ------------------------------------------------------------------ the cell operator
-// Loads the stencil of cell c (i,j) into shared memory and computes, per coefficient,
-// R_ij(f) - r_ij.  On return the threads own elements o = tid, tid + kThreads, ... of the
-// result through the callback `emit(o, R_o - r_o)`.  `coherent` selects L2-only loads (the
-// sweep kernel reads cells other CTAs have just written).
+// Loads the stencil of cell c (i,j) and computes, per coefficient, R_ij(f) - r_ij
+// (eq. ode-system in the cell basis).  Threads receive elements o = tid, tid + kThreads, ...
+// through emit(o, R_o - r_o).  kCoherent selects L2-only loads (the sweep kernel reads cells
+// other CTAs have just written).  Transform vector slots: 2f / 2f+1 = face f's left / right
+// state (E, W, N, S), or 2f = the cell re-expanded in the wall basis when face f is a wall;
+// slot 8 = r.
 template <bool kCoherent, typename Emit>
 __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, int i, int j, Emit emit) {
-  const int N = K.N, NP = K.NP, tid = threadIdx.x;
+  const int N = K.N, NP = K.NP, tid = threadIdx.x, W4 = 4 + NP;
   const int c = j * L.nx + i;
-  // ---- stencil existence and the wall faces
   if (tid < 9) {
     int ii = i + c_nb_di[tid], jj = j + c_nb_dj[tid];
     int reach = abs(c_nb_di[tid]) + abs(c_nb_dj[tid]);
     s.iarr[I_EX + tid] = (ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && reach <= K.reach) ? 1 : 0;
   }
   __syncthreads();
-  // ---- load the stencil (params + coefficients)
+  // ---- stencil (params + coefficients)
   for (int sl = 0; sl < 9; ++sl) {
     if (!s.iarr[I_EX + sl]) continue;
     int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
-    double *dst = s.st + sl * (4 + NP);
+    double *dst = stencil(s, sl, NP);
     const double *srcP = L.P + (size_t)cc * 4, *srcF = L.F + (size_t)cc * NP;
     for (int e = tid; e < 4 + N; e += kThreads) {
       const double *ptr = e < 4 ? srcP + e : srcF + (e - 4);
@@ -237,46 +254,61 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     }
   }
   if (tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
-  __syncthreads();
-  const double *pc = s.st;  // cell params, then coefficients at pc + 4
-  // ---- face states (eq. moments-recon) and the vectors to re-expand
-  for (int q = tid; q < 8 * (4 + N); q += kThreads) {
-    int v = q / (4 + N), e = q - v * (4 + N);
-    int f = v >> 1, side = v & 1;
-    bool wall = s.iarr[I_WALL + f];
-    if (wall && side) continue;
-    int ax = f >> 1;
-    double val;
-    if (wall) {
-      // the cell is wall-adjacent along this axis: zero slope, its face state is its own state
-      val = s.st[e];
-    } else {
-      int sx = c_fs_x[v], sm = c_fs_m[v], sp = c_fs_p[v];
-      bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + sm] && s.iarr[I_EX + sp];
-      double h = ax == 0 ? L.dx : L.dy;
-      val = recon(K.slope, s.st[sm * (4 + NP) + e], s.st[sx * (4 + NP) + e], s.st[sp * (4 + NP) + e], on,
-                  c_fs_sd[v], h);
-    }
-    if (e < 4) {
-      s.vsrc[v * 4 + e] = val;
-      if (wall) {
-        int w = c_face_wall[f];
-        s.vdst[v * 4 + e] = e < 3 ? K.wall_u[w][e] : K.wall_theta[w];
-      } else {
-        s.vdst[v * 4 + e] = pc[e];
-      }
-    } else {
-      s.VA[v * NP + (e - 4)] = val;
-    }
-  }
   if (L.has_r) {
     for (int e = tid; e < 4 + N; e += kThreads) {
       if (e < 4) {
         s.vsrc[8 * 4 + e] = L.rP[(size_t)c * 4 + e];
-        s.vdst[8 * 4 + e] = pc[e];
       } else {
         s.VA[8 * NP + e - 4] = L.rF[(size_t)c * NP + e - 4];
       }
+    }
+  }
+  __syncthreads();
+  const double *pc = s.cst;  // cell params, coefficients at pc + 4
+  // ---- face states (eq. moments-recon): six slope items, each element computed once
+  //   item 0: C along x -> slot 0 (E left) and slot 3 (W right), or slot 2 (W wall)
+  //   item 1: C along y -> slot 4 (N left) and slot 7 (S right), or slot 6 (S wall)
+  //   items 2..5: E -> slot 1, W -> slot 2, N -> slot 5, S -> slot 6
+  for (int q = tid; q < 6 * (4 + N); q += kThreads) {
+    int it = q / (4 + N), e = q - it * (4 + N);
+    int X = c_it_x[it], Xm = c_it_m[it], Xp = c_it_p[it];
+    if (!s.iarr[I_EX + X]) continue;
+    bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + Xm] && s.iarr[I_EX + Xp];
+    double q0 = stencil(s, X, NP)[e];
+    double hs = on ? half_slope(K.slope, stencil(s, Xm, NP)[e], q0, stencil(s, Xp, NP)[e]) : 0.0;
+    int v0, v1 = -1;
+    double x0, x1 = 0.0;
+    switch (it) {
+      case 0:
+        v0 = 0; x0 = q0 + hs;
+        if (s.iarr[I_WALL + 1]) { v1 = 2; x1 = q0; } else { v1 = 3; x1 = q0 - hs; }
+        break;
+      case 1:
+        v0 = 4; x0 = q0 + hs;
+        if (s.iarr[I_WALL + 3]) { v1 = 6; x1 = q0; } else { v1 = 7; x1 = q0 - hs; }
+        break;
+      case 2: v0 = 1; x0 = q0 - hs; break;
+      case 3: v0 = 2; x0 = q0 + hs; break;
+      case 4: v0 = 5; x0 = q0 - hs; break;
+      default: v0 = 6; x0 = q0 + hs; break;
+    }
+    if (e < 4) {
+      s.vsrc[v0 * 4 + e] = x0;
+      if (v1 >= 0) s.vsrc[v1 * 4 + e] = x1;
+    } else {
+      s.VA[v0 * NP + e - 4] = x0;
+      if (v1 >= 0) s.VA[v1 * NP + e - 4] = x1;
+    }
+  }
+  // destination bases: the cell, or the wall for a wall face's slot 2f
+  if (tid < 4 * kNV) {
+    int v = tid >> 2, e = tid & 3;
+    int f = v >> 1;
+    if (v < 8 && s.iarr[I_WALL + f] && !(v & 1)) {
+      int w = c_face_wall[f];
+      s.vdst[v * 4 + e] = e < 3 ? K.wall_u[w][e] : K.wall_theta[w];
+    } else {
+      s.vdst[v * 4 + e] = pc[e];
     }
   }
   if (tid == 0) {
@@ -288,29 +320,48 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     if (L.has_r) s.iarr[I_ACT + na++] = 8;
     s.iarr[I_NACT] = na;
   }
-  __syncthreads();
-  // ---- scalars: HLL speed bounds, collision frequency, Shakhov heat flux
-  if (tid < 4 && !s.iarr[I_WALL + tid]) {
-    int ax = tid >> 1;
-    const double *pm = s.vsrc + (2 * tid) * 4, *pp = s.vsrc + (2 * tid + 1) * 4;
-    s.sc[S_SLR + 2 * tid] = fmin(pm[ax] - K.C * sqrt(pm[3]), pp[ax] - K.C * sqrt(pp[3]));
-    s.sc[S_SLR + 2 * tid + 1] = fmax(pm[ax] + K.C * sqrt(pm[3]), pp[ax] + K.C * sqrt(pp[3]));
-  }
   if (tid == 32) {
     const double *f = pc + 4;
     double rho = f[0], th = pc[3];
     s.sc[S_NU] = K.beta * sqrt(M_PI / 2.0) * rho * pow(th, 1.0 - K.omega) / K.Kn;
     double sq = sqrt(th);
-    s.sc[S_DT] = K.cfl / ((fabs(pc[0]) + K.C * sq) / L.dx + (fabs(pc[1]) + K.C * sq) / L.dy);
+    s.sc[S_DT] = K.cfl / ((fabs(pc[0]) + K.C * sq) * L.idx + (fabs(pc[1]) + K.C * sq) * L.idy);
   }
-  if (tid >= 64 && tid < 67 && K.model == 1) {
-    // q_i = 2 f_{3e_i} + sum_d f_{2e_d + e_i} (eq. moments-relation); indices are in tshak's tail
-    int ii = tid - 64;
+  if (tid == 64) {
+    double it = 1.0 / pc[3], t = 1.0;
+    for (int k = 0; k <= K.M; ++k) {
+      s.sc[S_TPOW + k] = t;
+      t *= it;
+    }
+  }
+  if (tid >= 96 && tid < 99 && K.model == 1) {
+    // q_i = 2 f_{3e_i} + sum_d f_{2e_d + e_i} (eq. moments-relation)
+    int ii = tid - 96;
     const double *f = pc + 4;
-    const int *iq = K.tab_i32 + 4 * N + 4 * ii;  // idx(3e_i), idx(2e_0+e_i), idx(2e_1+e_i), idx(2e_2+e_i)
+    const int *iq = K.tab_i32 + 4 * N + 4 * ii;
     double q = 2.0 * f[iq[0]];
     for (int d = 0; d < 3; ++d) q += f[iq[1 + d]];
     s.sc[S_Q + ii] = q;
+  }
+  __syncthreads();
+  // ---- HLL weights per interior face: F = w1 Xi a- + w2 Xi a+ + w3 (a+ - a-)
+  if (tid < 4 && !s.iarr[I_WALL + tid]) {
+    int ax = tid >> 1;
+    const double *pm = s.vsrc + (2 * tid) * 4, *pp = s.vsrc + (2 * tid + 1) * 4;
+    double sL = fmin(pm[ax] - K.C * sqrt(pm[3]), pp[ax] - K.C * sqrt(pp[3]));
+    double sR = fmax(pm[ax] + K.C * sqrt(pm[3]), pp[ax] + K.C * sqrt(pp[3]));
+    double w1, w2, w3;
+    if (sL >= 0.0) {
+      w1 = 1.0; w2 = 0.0; w3 = 0.0;
+    } else if (sR <= 0.0) {
+      w1 = 0.0; w2 = 1.0; w3 = 0.0;
+    } else {
+      double inv = 1.0 / (sR - sL);
+      w1 = sR * inv; w2 = -sL * inv; w3 = sL * sR * inv;
+    }
+    s.sc[S_W + 3 * tid] = w1;
+    s.sc[S_W + 3 * tid + 1] = w2;
+    s.sc[S_W + 3 * tid + 2] = w3;
   }
   setup_coeffs(K, s);
   __syncthreads();
@@ -366,66 +417,72 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
       transform_batch(K, s, s.VA, s.VB);
     }
   }
-  // ---- assemble R = -(F_E - F_W)/dx - (F_N - F_S)/dy + Q (eq. ode-system)
+  // ---- flux differences per axis: F_E - F_W = Xi_x d_x + e_x, F_N - F_S = Xi_y d_y + e_y
+  //      with d = sum_f sign_f (w1 a- + w2 a+), e = sum_f sign_f w3 (a+ - a-) (+ wall fluxes)
+  double *dX = s.VA, *dY = s.VA + NP, *eX = s.VA + 2 * NP, *eY = s.VA + 3 * NP;
+  for (int o = tid; o < N; o += kThreads) {
+    double d[2] = {0.0, 0.0}, ee[2] = {0.0, 0.0};
+#pragma unroll
+    for (int fc = 0; fc < 4; ++fc) {
+      int ax = fc >> 1;
+      double sg = (fc & 1) ? -1.0 : 1.0;
+      if (s.iarr[I_WALL + fc]) {
+        ee[ax] = fma(sg, s.VB[(2 * fc) * NP + o], ee[ax]);
+      } else {
+        double am = s.VB[(2 * fc) * NP + o], ap = s.VB[(2 * fc + 1) * NP + o];
+        double w1 = s.sc[S_W + 3 * fc], w2 = s.sc[S_W + 3 * fc + 1], w3 = s.sc[S_W + 3 * fc + 2];
+        d[ax] = fma(sg, fma(w1, am, w2 * ap), d[ax]);
+        ee[ax] = fma(sg * w3, ap - am, ee[ax]);
+      }
+    }
+    dX[o] = d[0];
+    dY[o] = d[1];
+    eX[o] = ee[0];
+    eY[o] = ee[1];
+  }
+  __syncthreads();
+  // ---- R = -(F_E - F_W)/dx - (F_N - F_S)/dy + Q
   const double *f = pc + 4;
   const double nu = s.sc[S_NU];
   for (int o = tid; o < N; o += kThreads) {
-    double Ff[4];
+    double xi[2];
 #pragma unroll
-    for (int fc = 0; fc < 4; ++fc) {
-      if (s.iarr[I_WALL + fc]) {
-        Ff[fc] = s.VB[(2 * fc) * NP + o];
-      } else {
-        int ax = fc >> 1;
-        const double *am = s.VB + (2 * fc) * NP, *ap = s.VB + (2 * fc + 1) * NP;
-        uint16_t pr = s.tprev[ax * N + o], nx = s.tnext[ax * N + o];
-        double al1 = (double)(s.tal[ax * N + o] + 1);
-        double xm = pc[ax] * am[o], xp = pc[ax] * ap[o];
-        if (pr != kNone) {
-          xm += pc[3] * am[pr];
-          xp += pc[3] * ap[pr];
-        }
-        if (nx != kNone) {
-          xm += al1 * am[nx];
-          xp += al1 * ap[nx];
-        }
-        double sL = s.sc[S_SLR + 2 * fc], sR = s.sc[S_SLR + 2 * fc + 1];
-        if (sL >= 0.0)
-          Ff[fc] = xm;
-        else if (sR <= 0.0)
-          Ff[fc] = xp;
-        else
-          Ff[fc] = (sR * xm - sL * xp + sL * sR * (ap[o] - am[o])) / (sR - sL);
-      }
+    for (int ax = 0; ax < 2; ++ax) {
+      const double *dd = ax == 0 ? dX : dY;
+      uint16_t pr = s.tprev[ax * N + o], nx = s.tnext[ax * N + o];
+      double v = pc[ax] * dd[o];
+      if (pr != kNone) v = fma(pc[3], dd[pr], v);
+      if (nx != kNone) v = fma((double)(s.tal[ax * N + o] + 1), dd[nx], v);
+      xi[ax] = v;
     }
     double fE = 0.0;
     if (o == 0) {
       fE = f[0];
     } else if (K.model == 1) {
       int t = s.tshak[o];
-      if (t >= 0) fE = (1.0 - K.Pr) * s.sc[S_Q + t] / 5.0;
+      if (t >= 0) fE = (1.0 - K.Pr) * s.sc[S_Q + t] * 0.2;
     }
     double Q = nu * (fE - f[o]);
-    double R = -(Ff[0] - Ff[1]) / L.dx - (Ff[2] - Ff[3]) / L.dy + Q;
+    double R = fma(-(xi[0] + eX[o]), L.idx, fma(-(xi[1] + eY[o]), L.idy, Q));
     double r = L.has_r ? s.VB[8 * NP + o] : 0.0;
     emit(o, R - r);
   }
 }
 
 // Back to Grad form (Sec. 2.4): macroscopics of g (basis pc), project g into the new basis,
-// zero f_{e_d} and the round-off mean of f_{2e_d}.  g lives in VA slot 0; the result is left in
-// VB slot 0 and the new params in sc[S_NEWP..].  Returns true when the state is physical.
-__device__ inline bool regrad(const Consts &K, Sm &s, const double *pc) {
-  const int tid = threadIdx.x;
+// zero f_{e_d} and the round-off mean of f_{2e_d}.  g lives in VA slot `v`; the result is left
+// in VB slot `v` and the new params in sc[S_NEWP..].  Returns true when the state is physical.
+__device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v) {
+  const int tid = threadIdx.x, NP = K.NP;
   if (tid == 0) {
     double mac[5];
-    macros(K, pc, s.VA, mac);
+    macros(K, pc, s.VA + v * NP, mac);
     for (int e = 0; e < 4; ++e) {
       s.sc[S_NEWP + e] = mac[1 + e];
-      s.vsrc[e] = pc[e];
-      s.vdst[e] = mac[1 + e];
+      s.vsrc[v * 4 + e] = pc[e];
+      s.vdst[v * 4 + e] = mac[1 + e];
     }
-    s.iarr[I_ACT] = 0;
+    s.iarr[I_ACT] = v;
     s.iarr[I_NACT] = 1;
     s.iarr[I_BAD] = !(isfinite(mac[0]) && isfinite(mac[4]) && mac[0] > 0.0 && mac[4] > 0.0);
   }
@@ -433,15 +490,15 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc) {
   setup_coeffs(K, s);
   __syncthreads();
   transform_batch(K, s, s.VA, s.VB);
+  double *g = s.VB + v * NP;
   if (tid == 0) {
-    double *g = s.VB;
     for (int d = 0; d < 3; ++d) g[K.idx_e[d]] = 0.0;
     double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) / 3.0;
     for (int d = 0; d < 3; ++d) g[K.idx_2e[d]] -= s3;
   }
   __syncthreads();
   int bad = 0;
-  for (int o = tid; o < K.N; o += kThreads) bad |= !isfinite(s.VB[o]);
+  for (int o = tid; o < K.N; o += kThreads) bad |= !isfinite(g[o]);
   bad = __syncthreads_or(bad);
   return !(bad || s.iarr[I_BAD]);
 }
@@ -511,14 +568,14 @@ __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int 
     __syncthreads();
     if (s.iarr[I_ABORT]) break;
     // ---- R_ij(f) - r_ij, then f + dt (R - r) into VA slot 0
-    cell_residual<true>(K, L, s, i, j, [&](int o, double Rr) { s.VA[o] = s.st[4 + o] + s.sc[S_DT] * Rr; });
+    cell_residual<true>(K, L, s, i, j,
+                        [&](int o, double Rr) { s.VA[4 * NP + o] = fma(s.sc[S_DT], Rr, s.cst[4 + o]); });
     __syncthreads();
-    // copy the cell's params (stencil slot 0 is overwritten by nothing below, but keep a copy)
     double pcell[4];
-    for (int e = 0; e < 4; ++e) pcell[e] = s.st[e];
-    bool ok = regrad(K, s, pcell);
+    for (int e = 0; e < 4; ++e) pcell[e] = s.cst[e];
+    bool ok = regrad(K, s, pcell, 4);
     double *Fo = L.F + (size_t)c * NP;
-    for (int o = tid; o < N; o += kThreads) Fo[o] = s.VB[o];
+    for (int o = tid; o < N; o += kThreads) Fo[o] = s.VB[4 * NP + o];
     if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
     if (!ok && tid == 0) raise_status(K, kStNonPhysical, true);
     __syncthreads();
@@ -546,8 +603,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L
     if (mode == kResOut) {
       cell_residual<false>(K, L, s, i, j, [&](int o, double Rr) {
         if (out) out[(size_t)c * out_stride + o] = Rr;
-        double th = s.st[3];
-        double w = s.fact[o] * pow(th, -(double)s.tdeg[o]);
+        double w = s.fact[o] * s.sc[S_TPOW + s.tdeg[o]];
         loc += w * Rr * Rr;
       });
       double t = block_sum(loc, s.sc + S_RED);
@@ -679,7 +735,7 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(Consts K, LevelDev Lf
     __syncthreads();
     double pcell[4];
     for (int e = 0; e < 4; ++e) pcell[e] = s.sc[S_PH + e];
-    bool ok = regrad(K, s, pcell);
+    bool ok = regrad(K, s, pcell, 0);
     for (int o = tid; o < N; o += kThreads) Lf.F[(size_t)c * NP + o] = s.VB[o];
     if (tid < 4) Lf.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
     if (!ok && tid == 0) raise_status(K, kStNonPhysical, false);
