@@ -20,7 +20,9 @@
  *   descending), N_M = (M+1)(M+2)(M+3)/6 doubles.  States handed to the
  *   library must be in Grad form (f_0 = rho > 0, f_{e_d} = 0,
  *   sum_d f_{2e_d} = 0, theta > 0), planar (u3 = 0 and f_alpha = 0 for odd
- *   alpha_3: the symmetry of a flow with d/dx3 = 0).
+ *   alpha_3: the symmetry of a flow with d/dx3 = 0).  Planar states stay planar
+ *   exactly, so the kernels form only the coefficients with even alpha_3; the
+ *   calls that take a state or a right-hand side reject non-planar input.
  * Device arrays are row-major: params [cells][4], coefficients
  *   [cells][N_M] (dense, no padding), all FP64.
  * Walls: index 0 bottom (y = 0), 1 right (x = lx), 2 top (y = ly),
@@ -116,7 +118,9 @@ nrmg_status nrmg_destroy(nrmg_ctx *ctx);
 
 /* Copy a state (device arrays, layout above) into level `level`.  Setting
  * the finest level also resets the reference mass of the mass correction and
- * the reference residual ||R(f^0)|| of eq. (relative-residual). */
+ * the reference residual ||R(f^0)|| of eq. (relative-residual).  Synchronizes.
+ * Errors: NRMG_ERR_ARG for a non-planar state, NRMG_ERR_NONPHYSICAL for
+ * rho <= 0, theta <= 0 or a non-finite value (the level is then undefined). */
 nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *dev_params, const double *dev_coeffs);
 
 /* Copy level `level`'s state out to device arrays (either may be NULL). */
@@ -124,7 +128,9 @@ nrmg_status nrmg_get_state(nrmg_ctx *ctx, int level, double *dev_params, double 
 
 /* Set the right-hand side r of level `level` (the r of Algorithm 1),
  * expanded in the per-cell bases dev_rparams; NULL pointers clear it (r = 0).
- * Algorithm 2 overwrites the r of every level below the finest. */
+ * Algorithm 2 overwrites the r of every level below the finest.  Synchronizes.
+ * Errors: NRMG_ERR_ARG for a non-planar r, NRMG_ERR_NONPHYSICAL for a
+ * non-finite r or a basis with theta <= 0. */
 nrmg_status nrmg_set_rhs(nrmg_ctx *ctx, int level, const double *dev_rparams, const double *dev_rcoeffs);
 
 /* `steps` fast-sweeping steps FS(f, r) (Sec. 3.1, Algorithm 1) on level

@@ -17,10 +17,10 @@ namespace {
 
 // ------------------------------------------------------------------ index tables
 struct Tables {
-  int M = 0, N = 0;
+  int M = 0, N = 0, NE = 0;
   std::vector<int> al;           // [N][3]
-  std::vector<int32_t> i32;      // tslot[3N], tshak[N], iq[12], is[6]
-  std::vector<uint16_t> u16;     // tmem[3N], tprev[3N], tnext[3N], tal[3N], tdeg[N]
+  std::vector<int32_t> i32;      // tslot[3][NE], tshak[N], iq[12], is[6]
+  std::vector<uint16_t> u16;     // tmem[3N], tprev[3N], tnext[3N], tal[3N], tdeg[N], eidx[NE]
   std::vector<double> fact;      // [N]
   int idx_axis[2][kMaxM + 1];
   int idx_e[3], idx_2e[3];
@@ -48,9 +48,16 @@ void build_tables(int M, Tables &T) {
         T.al[3 * k + 2] = a3;
         cube[(a1 * (M + 1) + a2) * (M + 1) + a3] = k++;
       }
-  T.i32.assign(4 * N + 18, -1);
-  T.u16.assign(13 * N, 0xFFFF);
+  // the outputs formed by the kernels: multi-indices with even alpha_3 (planar states)
+  std::vector<int> even;
+  for (int o = 0; o < N; ++o)
+    if (T.al[3 * o + 2] % 2 == 0) even.push_back(o);
+  const int NE = (int)even.size();
+  T.NE = NE;
+  T.i32.assign(3 * NE + N + 18, -1);
+  T.u16.assign(13 * N + NE, 0xFFFF);
   T.fact.resize(N);
+  for (int q = 0; q < NE; ++q) T.u16[13 * N + q] = (uint16_t)even[q];
   for (int d = 0; d < 3; ++d) {
     // index lines along d: all alpha sharing alpha with alpha_d = 0, stored by ascending alpha_d
     std::vector<int> s0(N, -1);
@@ -67,13 +74,13 @@ void build_tables(int M, Tables &T) {
         s0[q] = pos++;
       }
     }
-    // outputs sorted by line position (alpha_d) descending: a warp runs equal-length loops
-    std::vector<int> ord(N);
-    for (int o = 0; o < N; ++o) ord[o] = o;
+    // outputs (even alpha_3) sorted by line position (alpha_d) descending: a warp runs
+    // equal-length loops
+    std::vector<int> ord(even);
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return T.al[3 * x + d] > T.al[3 * y + d]; });
-    for (int r = 0; r < N; ++r) {
+    for (int r = 0; r < NE; ++r) {
       int o = ord[r];
-      T.i32[d * N + r] = o | (s0[o] << 11) | (T.al[3 * o + d] << 22);
+      T.i32[d * NE + r] = o | (s0[o] << 11) | (T.al[3 * o + d] << 22);
     }
     for (int o = 0; o < N; ++o) {
       int t[3] = {T.al[3 * o], T.al[3 * o + 1], T.al[3 * o + 2]};
@@ -100,18 +107,18 @@ void build_tables(int M, Tables &T) {
       for (int d = 0; d < 3; ++d)
         if (d != i && a[i] == 1 && a[d] == 2 && a[0] + a[1] + a[2] == 3) sh = i;
     }
-    T.i32[3 * N + o] = sh;
+    T.i32[3 * NE + o] = sh;
   }
   // heat-flux indices iq[i] = {3e_i, 2e_0+e_i, 2e_1+e_i, 2e_2+e_i} and sigma indices e_i+e_j
   for (int i = 0; i < 3; ++i) {
     int e3[3] = {0, 0, 0};
     e3[i] = 3;
-    T.i32[4 * N + 4 * i] = cidx(e3[0], e3[1], e3[2]);
+    T.i32[3 * NE + N + 4 * i] = cidx(e3[0], e3[1], e3[2]);
     for (int d = 0; d < 3; ++d) {
       int t[3] = {0, 0, 0};
       t[d] += 2;
       t[i] += 1;
-      T.i32[4 * N + 4 * i + 1 + d] = cidx(t[0], t[1], t[2]);
+      T.i32[3 * NE + N + 4 * i + 1 + d] = cidx(t[0], t[1], t[2]);
     }
   }
   int q = 0;
@@ -120,7 +127,7 @@ void build_tables(int M, Tables &T) {
       int t[3] = {0, 0, 0};
       t[i] += 1;
       t[j] += 1;
-      T.i32[4 * N + 12 + q++] = cidx(t[0], t[1], t[2]);
+      T.i32[3 * NE + N + 12 + q++] = cidx(t[0], t[1], t[2]);
     }
   for (int ax = 0; ax < 2; ++ax)
     for (int m = 0; m <= kMaxM; ++m) {
@@ -276,10 +283,10 @@ struct nrmg_ctx {
 namespace {
 
 void layout(const nrmg_grid *g, int M, Carver &cv, nrmg_ctx *ctx) {
-  const int N = nmom(M), NP = pad4(N);
+  const int N = nmom(M), NP = pad4(N), NE = nmom_even(M);
   // tables
-  int32_t *ti = cv.take<int32_t>(4 * N + 18);
-  uint16_t *tu = cv.take<uint16_t>(13 * N);
+  int32_t *ti = cv.take<int32_t>(3 * NE + N + 18);
+  uint16_t *tu = cv.take<uint16_t>(13 * N + NE);
   double *tf = cv.take<double>(N);
   double *wW = cv.take<double>(4 * (M + 1) * (M + 1));
   double *wR = cv.take<double>(4 * (M + 1));
@@ -481,6 +488,8 @@ nrmg_status set_maxwellian(nrmg_ctx *ctx) {
     CK(cudaMemsetAsync(L.rP, 0, sizeof(double) * 4 * L.ncell, ctx->stream));
     CK(cudaMemsetAsync(L.rF, 0, sizeof(double) * ctx->NP * L.ncell, ctx->stream));
     CK(cudaMemsetAsync(L.D, 0, sizeof(double) * ctx->NP * L.ncell, ctx->stream));
+    CK(cudaMemsetAsync(L.bP, 0, sizeof(double) * 4 * L.ncell, ctx->stream));
+    CK(cudaMemsetAsync(L.bF, 0, sizeof(double) * ctx->NP * L.ncell, ctx->stream));
     CK(cudaMemcpy2DAsync(L.F, sizeof(double) * ctx->NP, ones.data(), sizeof(double), sizeof(double), L.ncell,
                          cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpy2DAsync(L.P + 3, sizeof(double) * 4, ones.data(), sizeof(double), sizeof(double), L.ncell,
@@ -553,6 +562,8 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
     K.M = M;
     K.N = ctx->N;
     K.NP = ctx->NP;
+    K.NE = nmom_even(M);
+    K.iq_off = 3 * K.NE + K.N;
     K.reach = (opts->order == 2 && opts->slope != 0) ? 2 : 1;
     K.slope = opts->order == 2 ? opts->slope : 0;
     K.model = coll->model;
@@ -634,9 +645,10 @@ nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *P, const doub
   LevelDev &L = ctx->lev[level];
   CK(cudaMemcpyAsync(L.P, P, sizeof(double) * 4 * L.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(launch_pack(F, ctx->N, L.F, ctx->NP, L.ncell, ctx->N, ctx->stream));
-  CK(launch_check_state(ctx->K, L.P, L.F, ctx->NP, L.ncell, ctx->stream));
+  CK(launch_check_state(ctx->K, L.P, L.F, ctx->NP, L.ncell, 0, ctx->stream));
   ctx->launches += 2;
   nrmg_status s = sync_status(ctx);
+  if (s == NRMG_ERR_ARG) return set_err(ctx, s, "set_state: state is not planar (u3 or an odd-alpha3 coefficient is nonzero)");
   if (s != NRMG_OK) return set_err(ctx, s, "set_state: non-physical or non-finite state");
   if (level == ctx->levels - 1) {
     // reference mass of the correction
@@ -671,7 +683,11 @@ nrmg_status nrmg_set_rhs(nrmg_ctx *ctx, int level, const double *rP, const doubl
   }
   CK(cudaMemcpyAsync(L.rP, rP, sizeof(double) * 4 * L.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(launch_pack(rF, ctx->N, L.rF, ctx->NP, L.ncell, ctx->N, ctx->stream));
-  ctx->launches += 1;
+  CK(launch_check_state(ctx->K, L.rP, L.rF, ctx->NP, L.ncell, 1, ctx->stream));
+  ctx->launches += 2;
+  nrmg_status s = sync_status(ctx);
+  if (s == NRMG_ERR_ARG) return set_err(ctx, s, "set_rhs: right-hand side is not planar");
+  if (s != NRMG_OK) return set_err(ctx, s, "set_rhs: non-finite right-hand side or theta <= 0");
   L.has_r = 1;
   return NRMG_OK;
 }
@@ -846,7 +862,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
     if (!(walls[w].theta > 0.0) || walls[w].chi < 0.0 || walls[w].chi > 1.0) return NRMG_ERR_ARG;
     if (walls[w].u[kWallAxis[w]] != 0.0 || walls[w].u[2] != 0.0) return NRMG_ERR_ARG;
   }
-  const int N = nmom(M), NP = pad4(N);
+  const int N = nmom(M), NP = pad4(N), NE = nmom_even(M);
   const long long ncell = (long long)grid->nx * grid->ny;
   // layout of the scratch: tables, control words, reduction scratch, padded copy of the state
   size_t used = 0;
@@ -856,8 +872,8 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
     used += bytes;
     return o;
   };
-  const size_t o_i32 = at((4 * N + 18) * sizeof(int32_t));
-  const size_t o_u16 = at(13 * N * sizeof(uint16_t));
+  const size_t o_i32 = at((3 * NE + N + 18) * sizeof(int32_t));
+  const size_t o_u16 = at((13 * N + NE) * sizeof(uint16_t));
   const size_t o_f64 = at(N * sizeof(double));
   const size_t o_W = at(4 * (M + 1) * (M + 1) * sizeof(double));
   const size_t o_R = at(4 * (M + 1) * sizeof(double));
@@ -882,6 +898,8 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   K.M = M;
   K.N = N;
   K.NP = NP;
+  K.NE = NE;
+  K.iq_off = 3 * NE + N;
   K.reach = (opts->order == 2 && opts->slope != 0) ? 2 : 1;
   K.slope = opts->order == 2 ? opts->slope : 0;
   K.model = coll->model;
@@ -942,7 +960,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   NA(cudaMemsetAsync(K.status, 0, 64 * sizeof(int), st));
   NA(cudaMemcpyAsync(L.P, dev_params, sizeof(double) * 4 * ncell, cudaMemcpyDeviceToDevice, st));
   NA(launch_pack(dev_coeffs, N, L.F, NP, L.ncell, N, st));
-  NA(launch_check_state(K, L.P, L.F, NP, L.ncell, st));
+  NA(launch_check_state(K, L.P, L.F, NP, L.ncell, 0, st));
   int occ = occupancy_cell(M, NP, 1);
   long long g = (long long)nsm * (occ < 1 ? 1 : occ);
   if (g > ncell) g = ncell;

@@ -34,6 +34,8 @@ struct LevelDev {
 // pointers to the index tables built by the host.
 struct Consts {
   int M, N, NP;
+  int NE;      // number of multi-indices with even alpha_3 (the only nonzero ones of a planar state)
+  int iq_off;  // offset in tab_i32 of the heat-flux and stress indices
   int reach;   // stencil reach: 1 (first order) or 2 (second order)
   int slope;   // 0 none, 1 central, 2 van Albada
   int model;
@@ -41,8 +43,8 @@ struct Consts {
   double lx, ly;
   double wall_u[4][3], wall_theta[4];
   // tables (global memory, copied to shared memory by each CTA)
-  const int *tab_i32;   // tslot[3][N], then tshak[N] (Shakhov target or -1)
-  const uint16_t *tab_u16;  // tmem[3][N], then tprev[3][N], tnext[3][N] (0xFFFF = none), tdeg[N]
+  const int *tab_i32;   // tslot[3][NE], tshak[N] (Shakhov target or -1), iq[3][4], is[6]
+  const uint16_t *tab_u16;  // tmem[3][N], tprev[3][N], tnext[3][N] (0xFFFF = none), tal[3][N], tdeg[N], eidx[NE]
   const double *tab_f64;    // fact[N] (alpha!)
   const double *wallW;      // [4][(M+1)^2]: W^s_{k,m}
   const double *wallRho;    // [4][M+1]
@@ -53,6 +55,13 @@ struct Consts {
   int *abort_flag;
   int *queue;
 };
+
+// Number of multi-indices |alpha| <= M with even alpha_3.
+__host__ __device__ inline int nmom_even(int M) {
+  int n = 0;
+  for (int a3 = 0; a3 <= M; a3 += 2) n += (M - a3 + 1) * (M - a3 + 2) / 2;
+  return n;
+}
 
 // Size in bytes of the dynamic shared memory of the cell kernels.
 size_t cell_smem_bytes(int M, int NP);
@@ -71,7 +80,9 @@ cudaError_t launch_mass(const Consts &K, const LevelDev &L, double *partials, in
 cudaError_t launch_fields(const Consts &K, const LevelDev &L, double *out, cudaStream_t st);
 cudaError_t launch_pack(const double *src, int src_stride, double *dst, int dst_stride, int rows, int cols,
                         cudaStream_t st);
-cudaError_t launch_check_state(const Consts &K, const double *P, const double *F, int stride, int ncell,
+// Admissibility of a state (rhs = 0) or of a right-hand side (rhs = 1) handed in through the C
+// ABI; records NRMG_ERR_ARG for a non-planar input, NRMG_ERR_NONPHYSICAL otherwise.
+cudaError_t launch_check_state(const Consts &K, const double *P, const double *F, int stride, int ncell, int rhs,
                                cudaStream_t st);
 int occupancy_cell(int M, int NP, int which);  // CTAs per SM of kernel `which` (0 fs, 1 res, 2 restrict, 3 prolong)
 

@@ -40,6 +40,7 @@ __host__ __device__ inline size_t vb_doubles(int NP) {
 constexpr int kScal = 128;  // doubles of per-cell scalars
 
 __host__ __device__ inline SLayout make_layout(int M, int N, int NP) {
+  const int NE = nmom_even(M);
   SLayout s;
   size_t o = 0;
   s.cst = o;   o = al16(o + sizeof(double) * (4 + NP));
@@ -50,10 +51,10 @@ __host__ __device__ inline SLayout make_layout(int M, int N, int NP) {
   s.cf = o;    o = al16(o + sizeof(double) * kNV * 3 * (M + 1));
   s.sc = o;    o = al16(o + sizeof(double) * kScal);
   s.fact = o;  o = al16(o + sizeof(double) * N);
-  s.ti32 = o;  o = al16(o + sizeof(int) * 4 * N);
+  s.ti32 = o;  o = al16(o + sizeof(int) * (3 * NE + N));
   s.vflag = o; o = al16(o + sizeof(int) * kNV * 3);
   s.iarr = o;  o = al16(o + sizeof(int) * 64);
-  s.tu16 = o;  o = al16(o + sizeof(uint16_t) * 13 * N);
+  s.tu16 = o;  o = al16(o + sizeof(uint16_t) * (13 * N + NE));
   s.total = o;
   return s;
 }
@@ -66,7 +67,7 @@ size_t cell_smem_bytes(int M, int NP) {
 struct Sm {
   double *cst, *VA, *VB, *vsrc, *vdst, *cf, *sc, *fact;
   int *tslot, *tshak, *vflag, *iarr;
-  uint16_t *tmem, *tprev, *tnext, *tal, *tdeg;
+  uint16_t *tmem, *tprev, *tnext, *tal, *tdeg, *eidx;
 };
 
 // iarr slots
@@ -91,7 +92,7 @@ __device__ inline Sm bind_smem(char *base, int M, int N, int NP) {
   s.sc = (double *)(base + L.sc);
   s.fact = (double *)(base + L.fact);
   s.tslot = (int *)(base + L.ti32);
-  s.tshak = s.tslot + 3 * N;
+  s.tshak = s.tslot + 3 * nmom_even(M);
   s.vflag = (int *)(base + L.vflag);
   s.iarr = (int *)(base + L.iarr);
   s.tmem = (uint16_t *)(base + L.tu16);
@@ -99,6 +100,7 @@ __device__ inline Sm bind_smem(char *base, int M, int N, int NP) {
   s.tnext = s.tmem + 6 * N;
   s.tal = s.tmem + 9 * N;
   s.tdeg = s.tmem + 12 * N;
+  s.eidx = s.tmem + 13 * N;
   return s;
 }
 
@@ -109,8 +111,8 @@ __device__ inline double *stencil(const Sm &s, int sl, int NP) {
 
 __device__ inline void load_tables(const Consts &K, Sm &s) {
   const int N = K.N;
-  for (int e = threadIdx.x; e < 4 * N; e += kThreads) s.tslot[e] = K.tab_i32[e];
-  for (int e = threadIdx.x; e < 13 * N; e += kThreads) s.tmem[e] = K.tab_u16[e];
+  for (int e = threadIdx.x; e < 3 * K.NE + N; e += kThreads) s.tslot[e] = K.tab_i32[e];
+  for (int e = threadIdx.x; e < 13 * N + K.NE; e += kThreads) s.tmem[e] = K.tab_u16[e];
   for (int e = threadIdx.x; e < N; e += kThreads) s.fact[e] = K.tab_f64[e];
 }
 
@@ -162,16 +164,19 @@ __device__ inline void setup_coeffs(const Consts &K, Sm &s) {
 
 // g = prod_d exp(-a_d S_d - b S_d^2) f for the active vectors: passes X->Y, Y->X, X->Y.
 // Output alpha of direction d sums c_k f_{alpha - k e_d}, k = 0..alpha_d; the index line of
-// alpha along d is stored contiguously in tmem (s0 = position of alpha itself).
+// alpha along d is stored contiguously in tmem (s0 = position of alpha itself).  Only the
+// outputs with even alpha_3 are formed: for planar states (u_3 = 0, odd alpha_3 coefficients
+// zero) the others stay exactly zero, and directions 1, 2 and the even-k direction-3 series
+// map even alpha_3 onto even alpha_3.
 __device__ inline void transform_batch(const Consts &K, Sm &s, double *X, double *Y) {
-  const int N = K.N, NP = K.NP, M = K.M, na = s.iarr[I_NACT];
+  const int N = K.N, NE = K.NE, NP = K.NP, M = K.M, na = s.iarr[I_NACT];
   for (int d = 0; d < 3; ++d) {
     const double *in = (d == 1) ? Y : X;
     double *out = (d == 1) ? X : Y;
-    const int *slot = s.tslot + d * N;
+    const int *slot = s.tslot + d * NE;
     const uint16_t *mem = s.tmem + d * N;
-    for (int q = threadIdx.x; q < na * N; q += kThreads) {
-      int vi = q / N, r = q - vi * N;
+    for (int q = threadIdx.x; q < na * NE; q += kThreads) {
+      int vi = q / NE, r = q - vi * NE;
       int v = s.iarr[I_ACT + vi];
       int pk = slot[r];
       int o = pk & 2047, s0 = (pk >> 11) & 2047, p = pk >> 22;
@@ -192,11 +197,12 @@ __device__ inline void transform_batch(const Consts &K, Sm &s, double *X, double
   }
 }
 
-// rho, u, theta of g in a general basis p (eq. rho-u-theta with the moments of H_alpha).
+// rho, u, theta of g in a general basis p (eq. rho-u-theta with the moments of H_alpha);
+// planar: f_{e_3} = 0.
 __device__ inline void macros(const Consts &K, const double *p, const double *g, double *out) {
   double rho = g[0], f2 = 0.0, fe2 = 0.0, fe[3];
   for (int d = 0; d < 3; ++d) {
-    fe[d] = g[K.idx_e[d]];
+    fe[d] = d < 2 ? g[K.idx_e[d]] : 0.0;
     f2 += g[K.idx_2e[d]];
     fe2 += fe[d] * fe[d];
   }
@@ -269,8 +275,10 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   //   item 0: C along x -> slot 0 (E left) and slot 3 (W right), or slot 2 (W wall)
   //   item 1: C along y -> slot 4 (N left) and slot 7 (S right), or slot 6 (S wall)
   //   items 2..5: E -> slot 1, W -> slot 2, N -> slot 5, S -> slot 6
-  for (int q = tid; q < 6 * (4 + N); q += kThreads) {
-    int it = q / (4 + N), e = q - it * (4 + N);
+  const int NE = K.NE;
+  for (int q = tid; q < 6 * (4 + NE); q += kThreads) {
+    int it = q / (4 + NE), e = q - it * (4 + NE);
+    if (e >= 4) e = 4 + s.eidx[e - 4];
     int X = c_it_x[it], Xm = c_it_m[it], Xp = c_it_p[it];
     if (!s.iarr[I_EX + X]) continue;
     bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + Xm] && s.iarr[I_EX + Xp];
@@ -338,7 +346,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     // q_i = 2 f_{3e_i} + sum_d f_{2e_d + e_i} (eq. moments-relation)
     int ii = tid - 96;
     const double *f = pc + 4;
-    const int *iq = K.tab_i32 + 4 * N + 4 * ii;
+    const int *iq = K.tab_i32 + K.iq_off + 4 * ii;
     double q = 2.0 * f[iq[0]];
     for (int d = 0; d < 3; ++d) q += f[iq[1 + d]];
     s.sc[S_Q + ii] = q;
@@ -381,10 +389,10 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     int nw = 0, wf[4];
     for (int f = 0; f < 4; ++f)
       if (s.iarr[I_WALL + f]) wf[nw++] = f;
-    for (int q = tid; q < nw * N; q += kThreads) {
-      int k = q / N, r = q - k * N;
+    for (int q = tid; q < nw * NE; q += kThreads) {
+      int k = q / NE, r = q - k * NE;
       int f = wf[k], w = c_face_wall[f], ax = c_wall_axis[w];
-      int pk = s.tslot[ax * N + r];
+      int pk = s.tslot[ax * NE + r];
       int o = pk & 2047, s0 = (pk >> 11) & 2047, p = pk >> 22;
       int b0 = s0 - p, deg = s.tdeg[o];
       int Lm = K.M - (deg - p);
@@ -420,7 +428,8 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   // ---- flux differences per axis: F_E - F_W = Xi_x d_x + e_x, F_N - F_S = Xi_y d_y + e_y
   //      with d = sum_f sign_f (w1 a- + w2 a+), e = sum_f sign_f w3 (a+ - a-) (+ wall fluxes)
   double *dX = s.VA, *dY = s.VA + NP, *eX = s.VA + 2 * NP, *eY = s.VA + 3 * NP;
-  for (int o = tid; o < N; o += kThreads) {
+  for (int q = tid; q < NE; q += kThreads) {
+    const int o = s.eidx[q];
     double d[2] = {0.0, 0.0}, ee[2] = {0.0, 0.0};
 #pragma unroll
     for (int fc = 0; fc < 4; ++fc) {
@@ -444,7 +453,8 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   // ---- R = -(F_E - F_W)/dx - (F_N - F_S)/dy + Q
   const double *f = pc + 4;
   const double nu = s.sc[S_NU];
-  for (int o = tid; o < N; o += kThreads) {
+  for (int q = tid; q < NE; q += kThreads) {
+    const int o = s.eidx[q];
     double xi[2];
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
@@ -492,13 +502,13 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v) {
   transform_batch(K, s, s.VA, s.VB);
   double *g = s.VB + v * NP;
   if (tid == 0) {
-    for (int d = 0; d < 3; ++d) g[K.idx_e[d]] = 0.0;
+    for (int d = 0; d < 2; ++d) g[K.idx_e[d]] = 0.0;  // f_{e_3} is not formed (odd alpha_3)
     double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) / 3.0;
     for (int d = 0; d < 3; ++d) g[K.idx_2e[d]] -= s3;
   }
   __syncthreads();
   int bad = 0;
-  for (int o = tid; o < K.N; o += kThreads) bad |= !isfinite(g[o]);
+  for (int q = tid; q < K.NE; q += kThreads) bad |= !isfinite(g[s.eidx[q]]);
   bad = __syncthreads_or(bad);
   return !(bad || s.iarr[I_BAD]);
 }
@@ -575,7 +585,10 @@ __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int 
     for (int e = 0; e < 4; ++e) pcell[e] = s.cst[e];
     bool ok = regrad(K, s, pcell, 4);
     double *Fo = L.F + (size_t)c * NP;
-    for (int o = tid; o < N; o += kThreads) Fo[o] = s.VB[4 * NP + o];
+    for (int q = tid; q < K.NE; q += kThreads) {
+      const int o = s.eidx[q];
+      Fo[o] = s.VB[4 * NP + o];
+    }
     if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
     if (!ok && tid == 0) raise_status(K, kStNonPhysical, true);
     __syncthreads();
@@ -606,6 +619,9 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L
         double w = s.fact[o] * s.sc[S_TPOW + s.tdeg[o]];
         loc += w * Rr * Rr;
       });
+      if (out)  // planar: the rows with odd alpha_3 are exactly zero
+        for (int o = tid; o < K.N; o += kThreads)
+          if (s.tal[2 * K.N + o] & 1) out[(size_t)c * out_stride + o] = 0.0;
       double t = block_sum(loc, s.sc + S_RED);
       if (tid == 0) acc += t * L.dx * L.dy;
     } else if (mode == kResDefect) {
@@ -625,14 +641,14 @@ __global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev L
   Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
   load_tables(K, s);
   __syncthreads();
-  const int tid = threadIdx.x, N = K.N, NP = K.NP;
+  const int tid = threadIdx.x, NE = K.NE, NP = K.NP;
   for (int C = blockIdx.x; C < Lc.ncell; C += gridDim.x) {
     const int I = C % Lc.nx, J = C / Lc.nx;
     int fi[4] = {(2 * J) * Lf.nx + 2 * I, (2 * J) * Lf.nx + 2 * I + 1, (2 * J + 1) * Lf.nx + 2 * I,
                  (2 * J + 1) * Lf.nx + 2 * I + 1};
-    // fine states into VA slots 0..3, fine defects into slots 4..7
-    for (int q = tid; q < 8 * N; q += kThreads) {
-      int v = q / N, o = q - v * N;
+    // fine states into VA slots 0..3, fine defects into slots 4..7 (even alpha_3 only)
+    for (int q = tid; q < 8 * NE; q += kThreads) {
+      int v = q / NE, o = s.eidx[q - v * NE];
       int cc = fi[v & 3];
       s.VA[v * NP + o] = v < 4 ? Lf.F[(size_t)cc * NP + o] : Lf.D[(size_t)cc * NP + o];
     }
@@ -669,7 +685,8 @@ __global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev L
     transform_batch(K, s, s.VA, s.VB);
     // area means (eq. fH)
     double *fH = s.VA, *RH = s.VA + NP;
-    for (int o = tid; o < N; o += kThreads) {
+    for (int q = tid; q < NE; q += kThreads) {
+      const int o = s.eidx[q];
       double a = 0.0, b = 0.0;
       for (int q = 0; q < 4; ++q) {
         a += s.VB[q * NP + o];
@@ -680,12 +697,13 @@ __global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev L
     }
     __syncthreads();
     if (tid == 0) {
-      for (int d = 0; d < 3; ++d) fH[K.idx_e[d]] = 0.0;
+      for (int d = 0; d < 2; ++d) fH[K.idx_e[d]] = 0.0;
       double s3 = (fH[K.idx_2e[0]] + fH[K.idx_2e[1]] + fH[K.idx_2e[2]]) / 3.0;
       for (int d = 0; d < 3; ++d) fH[K.idx_2e[d]] -= s3;
     }
     __syncthreads();
-    for (int o = tid; o < N; o += kThreads) {
+    for (int q = tid; q < NE; q += kThreads) {
+      const int o = s.eidx[q];
       Lc.F[(size_t)C * NP + o] = fH[o];
       Lc.bF[(size_t)C * NP + o] = fH[o];
       Lc.rF[(size_t)C * NP + o] = RH[o];
@@ -706,13 +724,13 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(Consts K, LevelDev Lf
   Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
   load_tables(K, s);
   __syncthreads();
-  const int tid = threadIdx.x, N = K.N, NP = K.NP;
+  const int tid = threadIdx.x, NE = K.NE, NP = K.NP;
   for (int c = blockIdx.x; c < Lf.ncell; c += gridDim.x) {
     const int i = c % Lf.nx, j = c / Lf.nx;
     const int C = (j / 2) * Lc.nx + i / 2;
     // slot 1: restricted coarse state, slot 2: current coarse state, both into the fine basis
-    for (int q = tid; q < 2 * N; q += kThreads) {
-      int v = q / N, o = q - v * N;
+    for (int q = tid; q < 2 * NE; q += kThreads) {
+      int v = q / NE, o = s.eidx[q - v * NE];
       s.VA[(1 + v) * NP + o] = v == 0 ? Lc.bF[(size_t)C * NP + o] : Lc.F[(size_t)C * NP + o];
     }
     if (tid < 8) {
@@ -730,13 +748,18 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(Consts K, LevelDev Lf
     setup_coeffs(K, s);
     __syncthreads();
     transform_batch(K, s, s.VA, s.VB);
-    for (int o = tid; o < N; o += kThreads)
+    for (int q = tid; q < NE; q += kThreads) {
+      const int o = s.eidx[q];
       s.VA[o] = (Lf.F[(size_t)c * NP + o] - s.VB[1 * NP + o]) + s.VB[2 * NP + o];
+    }
     __syncthreads();
     double pcell[4];
     for (int e = 0; e < 4; ++e) pcell[e] = s.sc[S_PH + e];
     bool ok = regrad(K, s, pcell, 0);
-    for (int o = tid; o < N; o += kThreads) Lf.F[(size_t)c * NP + o] = s.VB[o];
+    for (int q = tid; q < NE; q += kThreads) {
+      const int o = s.eidx[q];
+      Lf.F[(size_t)c * NP + o] = s.VB[o];
+    }
     if (tid < 4) Lf.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
     if (!ok && tid == 0) raise_status(K, kStNonPhysical, false);
     __syncthreads();
@@ -785,8 +808,8 @@ __global__ void mass_apply_kernel(LevelDev L, int NP, const double *scale) {
 __global__ void fields_kernel(Consts K, LevelDev L, double *out) {
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads) {
     const double *f = L.F + (size_t)c * K.NP, *p = L.P + (size_t)c * 4;
-    const int *iq = K.tab_i32 + 4 * K.N;       // [3][4] heat-flux indices
-    const int *is = K.tab_i32 + 4 * K.N + 12;  // [6] idx(e_i + e_j), i <= j
+    const int *iq = K.tab_i32 + K.iq_off;       // [3][4] heat-flux indices
+    const int *is = K.tab_i32 + K.iq_off + 12;  // [6] idx(e_i + e_j), i <= j
     double *o = out + (size_t)c * 14;
     o[0] = f[0];
     for (int d = 0; d < 3; ++d) o[1 + d] = p[d];
@@ -811,12 +834,19 @@ __global__ void pack_kernel(const double *src, int ss, double *dst, int ds, int 
   }
 }
 
-// Admissibility of a state handed in through the C ABI: rho > 0, theta > 0, finite.
-__global__ void check_state_kernel(Consts K, const double *P, const double *F, int stride, int ncell) {
+// Admissibility of a state (rhs = 0: rho > 0, theta > 0) or of a right-hand side (rhs = 1:
+// theta > 0) handed in through the C ABI: finite, and planar (u_3 = 0, odd alpha_3 zero).
+__global__ void check_state_kernel(Consts K, const double *P, const double *F, int stride, int ncell, int rhs) {
+  const uint16_t *a3 = K.tab_u16 + 9 * K.N + 2 * K.N;
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < ncell; c += gridDim.x * kThreads) {
     const double *p = P + (size_t)c * 4, *f = F + (size_t)c * stride;
-    bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(p[3]) && p[3] > 0.0 && f[0] > 0.0;
-    for (int o = 0; o < K.N && ok; ++o) ok = isfinite(f[o]);
+    bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[3]) && p[3] > 0.0 && (rhs || f[0] > 0.0);
+    bool planar = p[2] == 0.0;
+    for (int o = 0; o < K.N; ++o) {
+      ok = ok && isfinite(f[o]);
+      if (a3[o] & 1) planar = planar && f[o] == 0.0;
+    }
+    if (!planar) atomicCAS(K.status, 0, 1);
     if (!ok) atomicCAS(K.status, 0, kStNonPhysical);
   }
 }
@@ -897,11 +927,11 @@ cudaError_t launch_pack(const double *src, int src_stride, double *dst, int dst_
   return cudaGetLastError();
 }
 
-cudaError_t launch_check_state(const Consts &K, const double *P, const double *F, int stride, int ncell,
+cudaError_t launch_check_state(const Consts &K, const double *P, const double *F, int stride, int ncell, int rhs,
                                cudaStream_t st) {
   int g = (ncell + kThreads - 1) / kThreads;
   if (g > 4096) g = 4096;
-  check_state_kernel<<<g, kThreads, 0, st>>>(K, P, F, stride, ncell);
+  check_state_kernel<<<g, kThreads, 0, st>>>(K, P, F, stride, ncell, rhs);
   return cudaGetLastError();
 }
 

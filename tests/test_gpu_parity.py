@@ -210,6 +210,31 @@ def test_nonphysical_state_is_rejected():
     G.sync()  # the context stays usable
 
 
+def test_non_planar_input_is_rejected():
+    prob = lid_cavity(8, 4, 0.1, 0.1)
+    G = gpu(prob)
+    rng = np.random.default_rng(106)
+    P, F = random_state(rng, 8, 8, 4)
+    F2 = F.copy()
+    F2[3, 6] = 1e-3  # alpha = (1,0,1): odd alpha_3
+    with pytest.raises(nrmg.NrmgError) as e:
+        G.set_state(T(P), T(F2))
+    assert e.value.status == nrmg.ERR_ARG
+    P2 = P.copy()
+    P2[0, 2] = 0.01  # u_3 != 0
+    with pytest.raises(nrmg.NrmgError) as e:
+        G.set_state(T(P2), T(F))
+    assert e.value.status == nrmg.ERR_ARG
+    rP, rF = random_rhs(rng, 8, 8, 4)
+    rF[:, 6] = 1.0
+    with pytest.raises(nrmg.NrmgError) as e:
+        G.set_rhs(0, T(rP), T(rF))
+    assert e.value.status == nrmg.ERR_ARG
+    G.set_state(T(P), T(F))  # the context stays usable
+    R, n = G.residual(0)
+    assert np.isfinite(n) and np.all(N(R)[:, 6] == 0.0)
+
+
 @pytest.mark.parametrize("which", ["c2", "c3"])
 def test_full_size_residual_sampled(which):
     """The full-size cavity workloads (256x256 M=10; 512x512 M=8 Shakhov), launched as the
