@@ -256,6 +256,7 @@ def main():
         barrier()
     ms = e0.elapsed_time(e1)
     launches = S.launches - l0
+    per_level = S.fs_profile_levels()
     fs_ms, fs_n, u0, u1 = S.fs_profile()
     S.set_profiling(False)
     if world > 1:
@@ -326,6 +327,9 @@ def main():
                          "peak_source": "derived: SMs x 2 DFMA/clk x 2 flops x 2070 MHz (FP64 pipe)",
                          "fp64_fma_measured_tflops": fp64_peak_meas / 1e12,
                          "fs_ms_per_step": fs_ms / args.steps, "fs_launches": fs_n,
+                         "fs_ms_per_step_by_level": [round(m / args.steps, 3) for m, _ in per_level],
+                         "fs_us_per_cell_update_by_level": [round(1e3 * m / u, 3) if u else None
+                                                            for m, u in per_level],
                          "flops_per_cell_update": flops_per_update(w["M"], w["order"], False)},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "cell-moment updates/s", "h2d_bytes_per_step": bytes_state,

@@ -183,6 +183,9 @@ long long nrmg_launch_count(const nrmg_ctx *ctx);
  * event time in ms, the number of timed launches, and the cell updates they performed
  * without and with a right-hand side r (any pointer may be NULL), then resets the record. */
 nrmg_status nrmg_set_profiling(nrmg_ctx *ctx, int on);
+/* The same record split by level (arrays of `levels` entries: summed ms, cell updates);
+ * synchronizes and does not reset the record. */
+nrmg_status nrmg_fs_profile_levels(nrmg_ctx *ctx, double *ms_per_level, long long *updates_per_level);
 nrmg_status nrmg_fs_profile(nrmg_ctx *ctx, double *ms, long long *launches, long long *updates_no_r,
                             long long *updates_r);
 

@@ -234,6 +234,60 @@ void wall_tables(int M, const nrmg_wall *walls, std::vector<double> &W, std::vec
   }
 }
 
+// ------------------------------------------------------------------ sweep schedules
+// Cells of sweep Dk (k = 0..3 for D1..D4) by anti-diagonal, then by i.
+void sweep_order(int nx, int ny, int k, int *o) {
+  int n = 0;
+  bool idesc = (k == 1 || k == 2), jdesc = (k == 2 || k == 3);
+  for (int dg = 0; dg <= nx + ny - 2; ++dg)
+    for (int a = 0; a < nx; ++a) {
+      int b = dg - a;
+      if (b < 0 || b >= ny) continue;
+      int i = idesc ? nx - 1 - a : a, j = jdesc ? ny - 1 - b : b;
+      o[n++] = j * nx + i;
+    }
+}
+
+// Order of the items (s, k, c) of FS^steps by their earliest start in the dependency graph of
+// the exact sweep (longest path from the initial state, each update counted as one unit): the
+// update of cell c to version v = 4s + k + 1 depends on c's version v - 1 and on each cross
+// neighbour within `reach` at version v (visited before c by sweep Dk) or v - 1 (after).  The
+// order is topological, so CTAs taking items in this order never wait on an item not yet
+// taken, and items of consecutive sweeps and steps interleave as early as the serial order
+// allows.
+void asap_schedule(int nx, int ny, int reach, int steps, std::vector<int> &queue) {
+  const int nc = nx * ny, V = 4 * steps;
+  std::vector<int> tv((size_t)(V + 1) * nc, 0);
+  std::vector<int> ord(nc);
+  std::vector<std::pair<int, int>> keys;
+  keys.reserve((size_t)V * nc);
+  const int di[8] = {1, -1, 0, 0, 2, -2, 0, 0}, dj[8] = {0, 0, 1, -1, 0, 0, 2, -2};
+  const int nnb = reach == 2 ? 8 : 4;
+  for (int st = 0; st < steps; ++st)
+    for (int k = 0; k < 4; ++k) {
+      sweep_order(nx, ny, k, ord.data());
+      const int v = 4 * st + k + 1;
+      const int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
+      for (int n = 0; n < nc; ++n) {
+        const int c = ord[n], i = c % nx, j = c / nx;
+        int tmax = tv[(size_t)(v - 1) * nc + c];
+        for (int q = 0; q < nnb; ++q) {
+          int ii = i + di[q], jj = j + dj[q];
+          if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+          bool before = (si * di[q] < 0) || (di[q] == 0 && sj * dj[q] < 0);
+          int w = before ? v : v - 1;
+          tmax = std::max(tmax, tv[(size_t)w * nc + jj * nx + ii]);
+        }
+        tv[(size_t)v * nc + c] = tmax + 1;
+        keys.push_back({tmax + 1, (st * 4 + k) * nc + c});
+      }
+    }
+  std::stable_sort(keys.begin(), keys.end(),
+                   [](const std::pair<int, int> &a, const std::pair<int, int> &b) { return a.first < b.first; });
+  queue.resize(keys.size());
+  for (size_t q = 0; q < keys.size(); ++q) queue[q] = keys[q].second;
+}
+
 // ------------------------------------------------------------------ workspace layout
 struct Carver {
   size_t off = 0;
@@ -264,6 +318,11 @@ struct nrmg_ctx {
   int occ[4];
   Consts K;
   LevelDev lev[kMaxLev];
+  struct {
+    int steps;
+    int *queue;
+  } sched[kMaxLev][4];
+  int nsched[kMaxLev];
   double *partials, *dscal;   // reduction scratch, device scalars
   int *dstatus;
   double *hpin;               // pinned host scalars
@@ -276,13 +335,26 @@ struct nrmg_ctx {
   std::vector<cudaEvent_t> ev;
   std::vector<long long> ev_upd;   // cell updates of each timed launch
   std::vector<int> ev_hasr;
+  std::vector<int> ev_level;
   size_t ev_used;
   char err[256];
 };
 
 namespace {
 
-void layout(const nrmg_grid *g, int M, Carver &cv, nrmg_ctx *ctx) {
+// step counts with a precomputed schedule: 1 and the FS counts of Algorithm 2 on that level
+std::vector<int> sched_steps(int level, const nrmg_opts *o) {
+  std::vector<int> v = {1};
+  auto add = [&](int x) {
+    if (x > 0 && std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
+  };
+  if (level == 0) add(o->s3);
+  add(o->s1);
+  add(o->s2);
+  return v;
+}
+
+void layout(const nrmg_grid *g, int M, const nrmg_opts *opts, Carver &cv, nrmg_ctx *ctx) {
   const int N = nmom(M), NP = pad4(N), NE = nmom_even(M);
   // tables
   int32_t *ti = cv.take<int32_t>(3 * NE + N + 18);
@@ -316,6 +388,16 @@ void layout(const nrmg_grid *g, int M, Carver &cv, nrmg_ctx *ctx) {
     L.ver = cv.take<int>(nc);
     L.order = cv.take<int>(4 * nc);
     L.has_r = 0;
+    int ns = 0;
+    for (int steps : sched_steps(l, opts)) {
+      int *q = cv.take<int>((size_t)steps * 4 * nc);
+      if (ctx) {
+        ctx->sched[l][ns].steps = steps;
+        ctx->sched[l][ns].queue = q;
+      }
+      ++ns;
+    }
+    if (ctx) ctx->nsched[l] = ns;
   }
   if (ctx) {
     ctx->K.tab_i32 = ti;
@@ -397,13 +479,17 @@ nrmg_status smooth(nrmg_ctx *ctx, int level, int steps) {
   CK(cudaMemsetAsync(L.ver, 0, sizeof(int) * L.ncell, ctx->stream));
   CK(cudaMemsetAsync(ctx->K.queue, 0, sizeof(int), ctx->stream));
   int g = grid_for(ctx, 0, (long long)steps * 4 * L.ncell);
+  const int *queue = nullptr;
+  for (int q = 0; q < ctx->nsched[level]; ++q)
+    if (ctx->sched[level][q].steps == steps) queue = ctx->sched[level][q].queue;
   bool timed = ctx->profiling && ctx->ev_used + 2 <= ctx->ev.size();
   if (timed) CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
-  CK(launch_fs(ctx->K, L, steps, g, ctx->stream));
+  CK(launch_fs(ctx->K, L, steps, queue, g, ctx->stream));
   if (timed) {
     CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
     ctx->ev_upd[ctx->ev_used / 2] = (long long)steps * 4 * L.ncell;
     ctx->ev_hasr[ctx->ev_used / 2] = L.has_r;
+    ctx->ev_level[ctx->ev_used / 2] = level;
     ctx->ev_used += 2;
   }
   ctx->launches += 1;
@@ -509,7 +595,7 @@ extern "C" {
 size_t nrmg_workspace_bytes(const nrmg_grid *grid, int M, const nrmg_opts *opts) {
   if (!grid_ok(grid) || M < 3 || M > kMaxM || !opts_ok(opts)) return 0;
   Carver cv;
-  layout(grid, M, cv, nullptr);
+  layout(grid, M, opts, cv, nullptr);
   return cv.off + 256;
 }
 
@@ -546,7 +632,7 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
   ctx->ev_used = 0;
   Carver cv;
   cv.base = (char *)dev_workspace;
-  layout(grid, M, cv, ctx);
+  layout(grid, M, opts, cv, ctx);
 
   int dev = 0;
   nrmg_status s;
@@ -600,20 +686,16 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
     for (int l = 0; l < ctx->levels; ++l) {
       LevelDev &L = ctx->lev[l];
       std::vector<int> ord(4 * (size_t)L.ncell);
-      for (int k = 0; k < 4; ++k) {
-        int *o = ord.data() + (size_t)k * L.ncell;
-        int n = 0;
-        bool idesc = (k == 1 || k == 2), jdesc = (k == 2 || k == 3);
-        for (int dg = 0; dg <= L.nx + L.ny - 2; ++dg)
-          for (int a = 0; a < L.nx; ++a) {
-            int b = dg - a;
-            if (b < 0 || b >= L.ny) continue;
-            int i = idesc ? L.nx - 1 - a : a, j = jdesc ? L.ny - 1 - b : b;
-            o[n++] = j * L.nx + i;
-          }
-      }
+      for (int k = 0; k < 4; ++k) sweep_order(L.nx, L.ny, k, ord.data() + (size_t)k * L.ncell);
       CKF(cudaMemcpyAsync(L.order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st));
       CKF(cudaStreamSynchronize(st));
+      for (int q = 0; q < ctx->nsched[l]; ++q) {
+        std::vector<int> queue;
+        asap_schedule(L.nx, L.ny, K.reach, ctx->sched[l][q].steps, queue);
+        CKF(cudaMemcpyAsync(ctx->sched[l][q].queue, queue.data(), queue.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, st));
+        CKF(cudaStreamSynchronize(st));
+      }
     }
     for (int w = 0; w < 4; ++w) ctx->occ[w] = occupancy_cell(M, ctx->NP, w);
     if (ctx->occ[0] < 1) {
@@ -776,9 +858,26 @@ nrmg_status nrmg_set_profiling(nrmg_ctx *ctx, int on) {
     for (size_t k = 0; k < n; ++k) CK(cudaEventCreate(&ctx->ev[k]));
     ctx->ev_upd.assign(n / 2, 0);
     ctx->ev_hasr.assign(n / 2, 0);
+    ctx->ev_level.assign(n / 2, 0);
   }
   ctx->profiling = on ? 1 : 0;
   ctx->ev_used = 0;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_fs_profile_levels(nrmg_ctx *ctx, double *ms_per_level, long long *updates_per_level) {
+  if (!ctx || !ms_per_level || !updates_per_level) return NRMG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int l = 0; l < ctx->levels; ++l) {
+    ms_per_level[l] = 0.0;
+    updates_per_level[l] = 0;
+  }
+  for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]));
+    ms_per_level[ctx->ev_level[k / 2]] += t;
+    updates_per_level[ctx->ev_level[k / 2]] += ctx->ev_upd[k / 2];
+  }
   return NRMG_OK;
 }
 

@@ -67,7 +67,9 @@ __host__ __device__ inline int nmom_even(int M) {
 size_t cell_smem_bytes(int M, int NP);
 
 // Launchers (device translation unit).  Each returns cudaGetLastError().
-cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, int grid, cudaStream_t st);
+// FS^steps on level L.  queue (may be NULL): the order in which the persistent CTAs take the
+// steps*4*ncell items, each item (s*4 + k)*ncell + c; NULL = sweep by sweep in anti-diagonal order.
+cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, const int *queue, int grid, cudaStream_t st);
 cudaError_t launch_residual(const Consts &K, const LevelDev &L, int mode, double *out, int out_stride,
                             double *partials, int grid, cudaStream_t st);
 cudaError_t launch_restrict(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st);

@@ -526,7 +526,7 @@ __device__ inline double block_sum(double v, double *red) {
 }
 
 // ------------------------------------------------------------------ FS^steps (Algorithm 1)
-__global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int steps) {
+__global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int steps, const int *queue) {
   extern __shared__ __align__(16) char smem_raw[];
   Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
   load_tables(K, s);
@@ -543,10 +543,17 @@ __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int 
     __syncthreads();
     const long long item = s.iarr[I_ITEM];
     if (item >= total) break;
-    const int st = (int)(item / (4LL * ncell));
-    const int k = (int)((item / ncell) % 4);
-    const int n = (int)(item % ncell);
-    const int c = L.order[(size_t)k * ncell + n];
+    int st, k, c;
+    if (queue) {
+      const int qv = queue[item];
+      st = qv / (4 * ncell);
+      k = (qv / ncell) % 4;
+      c = qv % ncell;
+    } else {
+      st = (int)(item / (4LL * ncell));
+      k = (int)((item / ncell) % 4);
+      c = L.order[(size_t)k * ncell + (int)(item % ncell)];
+    }
     const int i = c % L.nx, j = c / L.nx;
     const int v = 4 * st + k + 1;  // the version this update produces
     // ---- wait until the cross stencil holds the versions of the serial order
@@ -868,9 +875,9 @@ static void ensure_smem_attr(Kern) {
 
 static size_t smem_for(const Consts &K) { return make_layout(K.M, K.N, K.NP).total; }
 
-cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, int grid, cudaStream_t st) {
+cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, const int *queue, int grid, cudaStream_t st) {
   ensure_smem_attr(fs_kernel);
-  fs_kernel<<<grid, kThreads, smem_for(K), st>>>(K, L, steps);
+  fs_kernel<<<grid, kThreads, smem_for(K), st>>>(K, L, steps, queue);
   return cudaGetLastError();
 }
 

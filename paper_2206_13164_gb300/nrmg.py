@@ -91,6 +91,8 @@ def lib():
         L.nrmg_fs_profile.restype = c_int
         L.nrmg_fs_profile.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
                                       POINTER(c_longlong)]
+        L.nrmg_fs_profile_levels.restype = c_int
+        L.nrmg_fs_profile_levels.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong)]
         L.nrmg_peak_fma.restype = c_int
         L.nrmg_peak_fma.argtypes = [c_int, c_int, c_void_p, POINTER(c_double)]
         L.nrmg_status_str.restype = ctypes.c_char_p
@@ -241,6 +243,13 @@ class Solver:
 
     def set_profiling(self, on: bool):
         self._check(self.L.nrmg_set_profiling(self.ctx, 1 if on else 0), "nrmg_set_profiling")
+
+    def fs_profile_levels(self):
+        """Per level: (ms, cell updates) of the timed FS launches (does not reset the record)."""
+        ms = (c_double * self.levels)()
+        up = (c_longlong * self.levels)()
+        self._check(self.L.nrmg_fs_profile_levels(self.ctx, ms, up), "nrmg_fs_profile_levels")
+        return [(ms[l], up[l]) for l in range(self.levels)]
 
     def fs_profile(self):
         """(ms, launches, cell updates without r, cell updates with r) of the timed FS launches."""
