@@ -147,7 +147,9 @@ __constant__ double c_inv[kMaxM + 2] = {1.0,       1.0 / 2,  1.0 / 3,  1.0 / 4, 
 
 // Coefficients of exp(-a z - b z^2) = sum_k c_k z^k for every active vector and direction:
 // c_0 = 1, c_1 = -a, (k+1) c_{k+1} = -a c_k - 2 b c_{k-1}, with a = w~_d - w_d, b = (t~ - t)/2.
-// Flags: bit 0 the direction is the identity, bit 1 a = 0 (odd c_k vanish exactly).
+// The factors -a/(k+1) and -2b/(k+1) do not depend on the chain, so each step costs one
+// dependent FMA.  Flags: bit 0 the direction is the identity, bit 1 a = 0 (odd c_k vanish
+// exactly).
 __device__ inline void setup_coeffs(const Consts &K, Sm &s) {
   const int M = K.M, na = s.iarr[I_NACT];
   for (int t = threadIdx.x; t < na * 3; t += kThreads) {
@@ -155,11 +157,37 @@ __device__ inline void setup_coeffs(const Consts &K, Sm &s) {
     double a = s.vdst[v * 4 + d] - s.vsrc[v * 4 + d];
     double b = 0.5 * (s.vdst[v * 4 + 3] - s.vsrc[v * 4 + 3]);
     double *c = s.cf + (v * 3 + d) * (M + 1);
-    c[0] = 1.0;
-    c[1] = -a;
-    for (int k = 1; k < M; ++k) c[k + 1] = (-a * c[k] - 2.0 * b * c[k - 1]) * c_inv[k];
+    double cm = 1.0, ck = -a;
+    c[0] = cm;
+    c[1] = ck;
+#pragma unroll
+    for (int k = 1; k < kMaxM; ++k) {
+      if (k >= M) break;
+      double u = (-2.0 * b * c_inv[k]) * cm;
+      double cn = fma(-a * c_inv[k], ck, u);
+      c[k + 1] = cn;
+      cm = ck;
+      ck = cn;
+    }
     s.vflag[v * 3 + d] = ((a == 0.0 && b == 0.0) ? 1 : 0) | (a == 0.0 ? 2 : 0);
   }
+}
+
+// one output coefficient of a directional pass: sum_k c_k x_{alpha - k e_d} over the
+// non-vanishing k, split over two accumulators so that two FMA chains run side by side
+__device__ inline double transform_one(const double *x, const double *c, const uint16_t *mem, int o, int s0, int p,
+                                       int fl) {
+  double a0 = x[o], a1 = 0.0;
+  if (!(fl & 1)) {
+    const int st = (fl & 2) ? 2 : 1;
+    int k = st;
+    for (; k + st <= p; k += 2 * st) {
+      a0 = fma(c[k], x[mem[s0 - k]], a0);
+      a1 = fma(c[k + st], x[mem[s0 - k - st]], a1);
+    }
+    if (k <= p) a0 = fma(c[k], x[mem[s0 - k]], a0);
+  }
+  return a0 + a1;
 }
 
 // g = prod_d exp(-a_d S_d - b S_d^2) f for the active vectors: passes X->Y, Y->X, X->Y.
@@ -167,31 +195,36 @@ __device__ inline void setup_coeffs(const Consts &K, Sm &s) {
 // alpha along d is stored contiguously in tmem (s0 = position of alpha itself).  Only the
 // outputs with even alpha_3 are formed: for planar states (u_3 = 0, odd alpha_3 coefficients
 // zero) the others stay exactly zero, and directions 1, 2 and the even-k direction-3 series
-// map even alpha_3 onto even alpha_3.
+// map even alpha_3 onto even alpha_3.  Each thread forms two outputs at a time (independent
+// FMA chains: dependent FP64 latency, not throughput, limits a single cell update).
 __device__ inline void transform_batch(const Consts &K, Sm &s, double *X, double *Y) {
   const int N = K.N, NE = K.NE, NP = K.NP, M = K.M, na = s.iarr[I_NACT];
+  const int tot = na * NE;
   for (int d = 0; d < 3; ++d) {
     const double *in = (d == 1) ? Y : X;
     double *out = (d == 1) ? X : Y;
     const int *slot = s.tslot + d * NE;
     const uint16_t *mem = s.tmem + d * N;
-    for (int q = threadIdx.x; q < na * NE; q += kThreads) {
+    for (int q = threadIdx.x; q < tot; q += 2 * kThreads) {
+      const int q2 = q + kThreads;
       int vi = q / NE, r = q - vi * NE;
       int v = s.iarr[I_ACT + vi];
       int pk = slot[r];
-      int o = pk & 2047, s0 = (pk >> 11) & 2047, p = pk >> 22;
-      const double *x = in + v * NP;
-      int fl = s.vflag[v * 3 + d];
-      double acc = x[o];
-      if (!(fl & 1)) {
-        const double *c = s.cf + (v * 3 + d) * (M + 1);
-        if (fl & 2) {
-          for (int k = 2; k <= p; k += 2) acc = fma(c[k], x[mem[s0 - k]], acc);
-        } else {
-          for (int k = 1; k <= p; ++k) acc = fma(c[k], x[mem[s0 - k]], acc);
-        }
+      int o = pk & 2047;
+      double y0 = transform_one(in + v * NP, s.cf + (v * 3 + d) * (M + 1), mem, o, (pk >> 11) & 2047, pk >> 22,
+                                s.vflag[v * 3 + d]);
+      double y1 = 0.0;
+      int v2 = 0, o2 = 0;
+      if (q2 < tot) {
+        int vi2 = q2 / NE, r2 = q2 - vi2 * NE;
+        v2 = s.iarr[I_ACT + vi2];
+        int pk2 = slot[r2];
+        o2 = pk2 & 2047;
+        y1 = transform_one(in + v2 * NP, s.cf + (v2 * 3 + d) * (M + 1), mem, o2, (pk2 >> 11) & 2047, pk2 >> 22,
+                           s.vflag[v2 * 3 + d]);
       }
-      out[v * NP + o] = acc;
+      out[v * NP + o] = y0;
+      if (q2 < tot) out[v2 * NP + o2] = y1;
     }
     __syncthreads();
   }
@@ -201,14 +234,15 @@ __device__ inline void transform_batch(const Consts &K, Sm &s, double *X, double
 // planar: f_{e_3} = 0.
 __device__ inline void macros(const Consts &K, const double *p, const double *g, double *out) {
   double rho = g[0], f2 = 0.0, fe2 = 0.0, fe[3];
+  const double ir = 1.0 / rho;
   for (int d = 0; d < 3; ++d) {
     fe[d] = d < 2 ? g[K.idx_e[d]] : 0.0;
     f2 += g[K.idx_2e[d]];
     fe2 += fe[d] * fe[d];
   }
   out[0] = rho;
-  for (int d = 0; d < 3; ++d) out[1 + d] = p[d] + fe[d] / rho;
-  out[4] = p[3] + (2.0 * f2 - fe2 / rho) / (3.0 * rho);
+  for (int d = 0; d < 3; ++d) out[1 + d] = fma(fe[d], ir, p[d]);
+  out[4] = fma(fma(2.0, f2, -fe2 * ir), ir * (1.0 / 3.0), p[3]);
 }
 
 // Half of the limited slope times the cell width, q_face = q0 +- hs (eq. moments-recon with the
@@ -276,11 +310,12 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   //   item 1: C along y -> slot 4 (N left) and slot 7 (S right), or slot 6 (S wall)
   //   items 2..5: E -> slot 1, W -> slot 2, N -> slot 5, S -> slot 6
   const int NE = K.NE;
-  for (int q = tid; q < 6 * (4 + NE); q += kThreads) {
+  // one slope item element: writes the face state(s) it feeds
+  auto face_item = [&](int q) {
     int it = q / (4 + NE), e = q - it * (4 + NE);
     if (e >= 4) e = 4 + s.eidx[e - 4];
     int X = c_it_x[it], Xm = c_it_m[it], Xp = c_it_p[it];
-    if (!s.iarr[I_EX + X]) continue;
+    if (!s.iarr[I_EX + X]) return;
     bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + Xm] && s.iarr[I_EX + Xp];
     double q0 = stencil(s, X, NP)[e];
     double hs = on ? half_slope(K.slope, stencil(s, Xm, NP)[e], q0, stencil(s, Xp, NP)[e]) : 0.0;
@@ -306,6 +341,13 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     } else {
       s.VA[v0 * NP + e - 4] = x0;
       if (v1 >= 0) s.VA[v1 * NP + e - 4] = x1;
+    }
+  };
+  {
+    const int tot = 6 * (4 + NE);
+    for (int q = tid; q < tot; q += 2 * kThreads) {
+      face_item(q);
+      if (q + kThreads < tot) face_item(q + kThreads);
     }
   }
   // destination bases: the cell, or the wall for a wall face's slot 2f
