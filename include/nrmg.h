@@ -91,7 +91,14 @@ typedef struct {
  *   cfl: CFL number of eq. (local-CFL) (the paper uses 0.9).
  *   s1, s2: pre/post FS steps, s3: FS steps of the coarsest solver, gamma: 1
  *     V-cycle, 2 W-cycle (Algorithm 2; the paper uses 2, 2, 4, 1).
- *   precision: 0 = FP64 throughout (the only value accepted). */
+ *   precision: 0 = FP64 throughout; 1 = mixed: on every level above the
+ *     coarsest, each FS^s of Algorithm 2 becomes one FP64 defect evaluation
+ *     d = r - R(f), s FP32 Gauss-Seidel steps (same cell order) on a
+ *     frozen-coefficient first-order linearization L e = d for the correction
+ *     e, and the FP64 update f <- Grad(f + e); the residual, the transfers, the
+ *     coarsest solve and the convergence test stay FP64, so the iteration
+ *     converges to the same FP64 fixed point R(f) = r.  nrmg_smooth always runs
+ *     the FP64 Algorithm 1. */
 typedef struct {
   int order, slope;
   double cfl;

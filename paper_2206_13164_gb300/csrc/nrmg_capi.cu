@@ -316,6 +316,7 @@ struct nrmg_ctx {
   cudaStream_t stream;
   int nsm;
   int occ[4];
+  int occ_corr;
   Consts K;
   LevelDev lev[kMaxLev];
   struct {
@@ -336,6 +337,7 @@ struct nrmg_ctx {
   std::vector<long long> ev_upd;   // cell updates of each timed launch
   std::vector<int> ev_hasr;
   std::vector<int> ev_level;
+  std::vector<int> ev_prec;   // 0 FP64 sweep, 1 FP32 correction sweep
   size_t ev_used;
   char err[256];
 };
@@ -363,6 +365,9 @@ void layout(const nrmg_grid *g, int M, const nrmg_opts *opts, Carver &cv, nrmg_c
   double *wW = cv.take<double>(4 * (M + 1) * (M + 1));
   double *wR = cv.take<double>(4 * (M + 1));
   double *wI = cv.take<double>(4 * (M + 1));
+  float *wWf = cv.take<float>(4 * (M + 1) * (M + 1));
+  float *wRf = cv.take<float>(4 * (M + 1));
+  float *wIf = cv.take<float>(4 * (M + 1));
   int *ctl = cv.take<int>(64);  // status, abort, queue
   double *part = cv.take<double>(kPartials);
   double *scal = cv.take<double>(64);
@@ -388,6 +393,13 @@ void layout(const nrmg_grid *g, int M, const nrmg_opts *opts, Carver &cv, nrmg_c
     L.ver = cv.take<int>(nc);
     L.order = cv.take<int>(4 * nc);
     L.has_r = 0;
+    if (opts->precision == 1) {
+      L.e32 = cv.take<float>(nc * NP);
+      L.d32 = cv.take<float>(nc * NP);
+      L.aux32 = cv.take<float>(nc * 8);
+    } else {
+      L.e32 = L.d32 = L.aux32 = nullptr;
+    }
     int ns = 0;
     for (int steps : sched_steps(l, opts)) {
       int *q = cv.take<int>((size_t)steps * 4 * nc);
@@ -406,6 +418,9 @@ void layout(const nrmg_grid *g, int M, const nrmg_opts *opts, Carver &cv, nrmg_c
     ctx->K.wallW = wW;
     ctx->K.wallRho = wR;
     ctx->K.wallIn = wI;
+    ctx->K.wallWf = wWf;
+    ctx->K.wallRf = wRf;
+    ctx->K.wallInf = wIf;
     ctx->K.status = ctl;
     ctx->K.abort_flag = ctl + 1;
     ctx->K.queue = ctl + 2;
@@ -431,7 +446,7 @@ bool opts_ok(const nrmg_opts *o) {
   if (o->order != 1 && o->order != 2) return false;
   if (o->slope < 0 || o->slope > 2) return false;
   if (!(o->cfl > 0.0) || o->s1 < 0 || o->s2 < 0 || o->s3 < 0 || o->gamma < 1 || o->gamma > 2) return false;
-  if (o->precision != 0) return false;
+  if (o->precision != 0 && o->precision != 1) return false;
   return true;
 }
 
@@ -490,6 +505,7 @@ nrmg_status smooth(nrmg_ctx *ctx, int level, int steps) {
     ctx->ev_upd[ctx->ev_used / 2] = (long long)steps * 4 * L.ncell;
     ctx->ev_hasr[ctx->ev_used / 2] = L.has_r;
     ctx->ev_level[ctx->ev_used / 2] = level;
+    ctx->ev_prec[ctx->ev_used / 2] = 0;
     ctx->ev_used += 2;
   }
   ctx->launches += 1;
@@ -542,17 +558,54 @@ nrmg_status two_grid_update(nrmg_ctx *ctx, int lf) {
   return NRMG_OK;
 }
 
+// Mixed-precision smoothing of level `level`: FP64 defect d = r - R(f), `steps` FP32 sweeps of
+// the linearized correction equation L e = d (same cell order as Algorithm 1), then
+// f <- Grad(f + e) in FP64.
+nrmg_status smooth_mixed(nrmg_ctx *ctx, int level, int steps) {
+  if (steps <= 0) return NRMG_OK;
+  LevelDev &L = ctx->lev[level];
+  nrmg_status s = residual(ctx, level, kResDefect, nullptr, 0, nullptr);
+  if (s != NRMG_OK) return s;
+  CK(launch_mixed_prep(ctx->K, L, ctx->stream));
+  CK(cudaMemsetAsync(L.ver, 0, sizeof(int) * L.ncell, ctx->stream));
+  CK(cudaMemsetAsync(ctx->K.queue, 0, sizeof(int), ctx->stream));
+  const int *queue = nullptr;
+  for (int q = 0; q < ctx->nsched[level]; ++q)
+    if (ctx->sched[level][q].steps == steps) queue = ctx->sched[level][q].queue;
+  long long g = (long long)ctx->nsm * std::max(1, ctx->occ_corr);
+  g = std::min<long long>(g, (long long)steps * 4 * L.ncell);
+  bool timed = ctx->profiling && ctx->ev_used + 2 <= ctx->ev.size();
+  if (timed) CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
+  CK(launch_fs_corr(ctx->K, L, steps, queue, (int)std::max(1LL, g), ctx->stream));
+  if (timed) {
+    CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
+    ctx->ev_upd[ctx->ev_used / 2] = (long long)steps * 4 * L.ncell;
+    ctx->ev_hasr[ctx->ev_used / 2] = L.has_r;
+    ctx->ev_level[ctx->ev_used / 2] = level;
+    ctx->ev_prec[ctx->ev_used / 2] = 1;
+    ctx->ev_used += 2;
+  }
+  CK(launch_mixed_update(ctx->K, L, grid_for(ctx, 3, L.ncell), ctx->stream));
+  ctx->launches += 3;
+  return NRMG_OK;
+}
+
+nrmg_status smooth_level(nrmg_ctx *ctx, int level, int steps) {
+  if (ctx->opts.precision == 1 && level > 0) return smooth_mixed(ctx, level, steps);
+  return smooth(ctx, level, steps);
+}
+
 // Algorithm 2 on level k
 nrmg_status nmg(nrmg_ctx *ctx, int k) {
   const nrmg_opts &o = ctx->opts;
   nrmg_status s;
   if (k == 0) return smooth(ctx, 0, o.s3);
-  if ((s = smooth(ctx, k, o.s1)) != NRMG_OK) return s;
+  if ((s = smooth_level(ctx, k, o.s1)) != NRMG_OK) return s;
   if ((s = two_grid_setup(ctx, k)) != NRMG_OK) return s;
   for (int g = 0; g < o.gamma; ++g)
     if ((s = nmg(ctx, k - 1)) != NRMG_OK) return s;
   if ((s = two_grid_update(ctx, k)) != NRMG_OK) return s;
-  return smooth(ctx, k, o.s2);
+  return smooth_level(ctx, k, o.s2);
 }
 
 nrmg_status mass_correct(nrmg_ctx *ctx) {
@@ -681,6 +734,13 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
     CKF(cudaMemcpyAsync((void *)K.wallW, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     CKF(cudaMemcpyAsync((void *)K.wallRho, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     CKF(cudaMemcpyAsync((void *)K.wallIn, In.data(), In.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    {
+      std::vector<float> Wf(W.begin(), W.end()), Rf(R.begin(), R.end()), If(In.begin(), In.end());
+      CKF(cudaMemcpyAsync((void *)K.wallWf, Wf.data(), Wf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      CKF(cudaMemcpyAsync((void *)K.wallRf, Rf.data(), Rf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      CKF(cudaMemcpyAsync((void *)K.wallInf, If.data(), If.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      CKF(cudaStreamSynchronize(st));
+    }
     CKF(cudaMemsetAsync(ctx->dstatus, 0, 64 * sizeof(int), st));
     // sweep orders: cells of Dk by anti-diagonal, then by i
     for (int l = 0; l < ctx->levels; ++l) {
@@ -698,6 +758,7 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
       }
     }
     for (int w = 0; w < 4; ++w) ctx->occ[w] = occupancy_cell(M, ctx->NP, w);
+    ctx->occ_corr = opts->precision == 1 ? occupancy_corr(M, ctx->NP) : 0;
     if (ctx->occ[0] < 1) {
       s = set_err(ctx, NRMG_ERR_ARG, "shared-memory footprint too large for this M");
       goto fail;
@@ -859,6 +920,7 @@ nrmg_status nrmg_set_profiling(nrmg_ctx *ctx, int on) {
     ctx->ev_upd.assign(n / 2, 0);
     ctx->ev_hasr.assign(n / 2, 0);
     ctx->ev_level.assign(n / 2, 0);
+    ctx->ev_prec.assign(n / 2, 0);
   }
   ctx->profiling = on ? 1 : 0;
   ctx->ev_used = 0;

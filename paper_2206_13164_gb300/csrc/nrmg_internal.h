@@ -28,6 +28,9 @@ struct LevelDev {
   int *ver;         // per-cell update counters of the sweep scheduler
   int *order;       // [4][ncell]: cells of sweep Dk in anti-diagonal order
   int has_r;
+  // FP32 correction sweeps (precision 1): correction e, FP64 defect rounded to FP32, and the
+  // frozen per-cell coefficients (u1, u2, u3, theta, dt, nu, 0, 0)
+  float *e32, *d32, *aux32;
 };
 
 // Everything a kernel needs besides the level: scheme constants and
@@ -49,6 +52,7 @@ struct Consts {
   const double *wallW;      // [4][(M+1)^2]: W^s_{k,m}
   const double *wallRho;    // [4][M+1]
   const double *wallIn;     // [4][M+1]
+  const float *wallWf, *wallRf, *wallInf;  // FP32 copies of the three wall tables
   int idx_axis[2][kMaxM + 1];  // index of m e_x, m e_y
   int idx_e[3], idx_2e[3];
   int *status;
@@ -87,5 +91,11 @@ cudaError_t launch_pack(const double *src, int src_stride, double *dst, int dst_
 cudaError_t launch_check_state(const Consts &K, const double *P, const double *F, int stride, int ncell, int rhs,
                                cudaStream_t st);
 int occupancy_cell(int M, int NP, int which);  // CTAs per SM of kernel `which` (0 fs, 1 res, 2 restrict, 3 prolong)
+
+// FP32 correction sweeps of the mixed-precision smoother (nrmg_mixed.cu).
+cudaError_t launch_mixed_prep(const Consts &K, const LevelDev &L, cudaStream_t st);
+cudaError_t launch_fs_corr(const Consts &K, const LevelDev &L, int steps, const int *queue, int grid, cudaStream_t st);
+cudaError_t launch_mixed_update(const Consts &K, const LevelDev &L, int grid, cudaStream_t st);
+int occupancy_corr(int M, int NP);
 
 }  // namespace nrmg

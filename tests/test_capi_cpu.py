@@ -55,7 +55,7 @@ def test_workspace_bytes_and_argument_checks():
         _args(M=2),                  # M >= 3 required
         _args(order=3),
         _args(slope=5),
-        _args(precision=1),          # only FP64 is accepted
+        _args(precision=2),          # 0 FP64, 1 mixed
     ]
     for g, M, o in bad:
         assert L.nrmg_workspace_bytes(ctypes.byref(g), M, ctypes.byref(o)) == 0

@@ -254,3 +254,31 @@ def test_full_size_residual_sampled(which):
     for i, j in cells:
         ro = O.cell_residual(top, int(i), int(j))
         assert_close(Rg[int(j) * prob.nx + int(i)], ro, 1e-12, f"cell {i},{j}")
+
+
+# ------------------------------------------------------------------ mixed precision (FP32 correction sweeps)
+@pytest.mark.parametrize("name,prob", [
+    ("lid_c1", None),
+    ("heated_o2", heated_cavity(16, 5, 0.3, order=2, slope=2, levels=2)),
+    ("lid_o2_M8", lid_cavity(32, 8, 0.05, 0.4, order=2, slope=2, levels=3)),
+])
+def test_mixed_precision_reaches_the_fp64_solution(name, prob):
+    """FP32 correction sweeps inside FP64 defect correction converge to the FP64 oracle's
+    discrete solution: relative residual 1e-8 (measured with the FP64 residual), fields within
+    the discrete solution's own tolerance (1e-6 relative to each field's scale)."""
+    from inputs import config_c1
+
+    prob = config_c1() if prob is None else prob
+    O = oracle_solver(prob)
+    sto, co, ro = O.solve(1e-8, 200)
+    assert sto == 0
+    G = nrmg.from_problem(prob, device=DEV, precision=1)
+    stg, cg, rg = G.solve(1e-8, 200)
+    assert stg == 0 and rg <= 1e-8
+    fg, fo = N(G.fields()), O.fields()
+    for k, nm in enumerate(FIELDS):
+        scale = max(np.abs(fo[..., k]).max(), 1e-3 * np.abs(fo[..., 0]).max())
+        assert np.abs(fg[..., k] - fo[..., k]).max() <= 1e-6 * scale, nm
+    # the residual the mixed form stops on is the FP64 residual of the same operator
+    _, n_final = G.residual()
+    assert n_final <= 1.0000001e-8 * O.res0()
