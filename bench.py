@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of the FAS/fast-sweeping moment solver on GB300.
 
-One step = one NMG V-cycle of Algorithm 2 (FS smoothing on every level, residual, restriction,
+One step = one NMG V-cycle of Algorithm 2 in FP64 (FS smoothing on every level, residual, restriction,
 coarse right-hand side, coarse-grid update), the mass correction and the residual norm, on the
 lid-driven cavity 256x256, M = 10 (286 moments), BGK, Kn = 0.01, lid velocity 0.5, second-order
 van Albada reconstruction, 6 levels (coarsest 8x8), s1 = s2 = 2, s3 = 4.
@@ -10,6 +10,10 @@ metric: cell-moment updates per second = 4 sweeps x cells x N_M per FS step, sum
 FS steps of every level in the timed cycles (residual evaluations are not counted).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload lid256|lid32|lid64|heat512]
+
+The JSON line also reports the same cycle with the mixed-precision smoother (FP32 correction
+sweeps inside FP64 defect correction) and, at N=1, the wall time of both forms to relative
+residual 1e-8 from the global Maxwellian.
 
 With --impl reference the CPU oracle (plain serial C) is timed on the host on a bounded sample
 of the same workload.  Multi-GPU runs (torchrun) solve one independent replica per GPU.
@@ -69,6 +73,12 @@ def cycle_updates(w):
         steps = 4  # s1 + s2 = 2 + 2 on levels >= 1, s3 = 4 on level 0
         tot += steps * 4 * cells * n
     return tot
+
+
+def flops_per_corr_update(M):
+    """FP32 flops of one correction-sweep cell update (first-order linearized operator, no
+    re-projection): 4 basis transforms + 60 flops per moment."""
+    return 4 * 6 * math.comb(M + 3, 4) + 60 * nmom(M)
 
 
 def flops_per_update(M, order, has_r):
@@ -206,6 +216,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lid256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-tol", action="store_true", help="skip the two solves to 1e-8")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision cycle timing")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -299,6 +311,59 @@ def main():
     e2e_value = cycle_updates(w) * e2e_steps * world / e2e_s
     bytes_state = (hP.numel() + hF.numel()) * 8
 
+    # mixed precision: FP32 correction sweeps inside FP64 defect correction, same cycle
+    mixed = None
+    if not args.no_mixed:
+        S2 = nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
+                         Pr=w["Pr"], order=w["order"], slope=w["slope"], precision=1, device=dev)
+        for _ in range(args.warmup):
+            S2.fas_cycle()
+        S2.set_profiling(True)
+        S2.fs_profile()
+        barrier()
+        torch.cuda.synchronize(dev)
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(S2.stream)
+        for _ in range(args.steps):
+            S2.fas_cycle()
+        m1.record(S2.stream)
+        torch.cuda.synchronize(dev)
+        mms = m0.elapsed_time(m1)
+        mlev = S2.fs_profile_levels()
+        cms, cn, cu0, cu1 = S2.fs_profile()
+        S2.set_profiling(False)
+        corr_fl = (cu0 + cu1) * flops_per_corr_update(w["M"])
+        fp32_peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+        mixed = {"value": cycle_updates(w) * args.steps * world / (mms * 1e-3), "unit": "cell-moment updates/s",
+                 "ms_per_step": mms / args.steps, "dtype": "f32 correction sweeps + f64 defect/transfers",
+                 "roofline": {"bound": "alu", "kernel": "fs_corr_kernel (FP32 correction sweeps, FS timings "
+                                                       "of all levels; the coarsest level stays FP64)",
+                              "achieved": corr_fl / (cms * 1e-3) / 1e12 if cms > 0 else None,
+                              "peak": fp32_peak, "unit": "TFLOP/s",
+                              "frac": (corr_fl / (cms * 1e-3) / 1e12 / fp32_peak) if cms > 0 else None,
+                              "peak_source": "derived: SMs x 128 FFMA/clk x 2 flops x 2070 MHz",
+                              "flops_per_cell_update": flops_per_corr_update(w["M"]),
+                              "sweep_ms_per_step": cms / args.steps,
+                              "sweep_ms_per_step_by_level": [round(m / args.steps, 3) for m, _ in mlev]}}
+        del S2
+
+    # time to relative residual 1e-8 from the global Maxwellian, plain FP64 vs mixed
+    ttt = None
+    if world == 1 and not args.no_time_to_tol:
+        ttt = {"tol": 1e-8}
+        for prec, key in ((0, "plain_fp64"), (1, "mixed")):
+            S3 = nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
+                             Pr=w["Pr"], order=w["order"], slope=w["slope"], precision=prec, device=dev)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            st, cyc, rr = S3.solve(1e-8, 400)
+            torch.cuda.synchronize(dev)
+            ttt[key] = {"seconds": time.perf_counter() - t0, "cycles": cyc, "rel_residual": rr,
+                        "status": int(st)}
+            del S3
+        ttt["mixed_over_plain_time"] = ttt["mixed"]["seconds"] / ttt["plain_fp64"]["seconds"]
+
     # roofline of the dominant kernel (the persistent FS sweep kernel, all levels)
     fl = u0 * flops_per_update(w["M"], w["order"], False) + u1 * flops_per_update(w["M"], w["order"], True)
     achieved = fl / (fs_ms * 1e-3) / 1e12 if fs_ms > 0 else None
@@ -336,6 +401,8 @@ def main():
                     "d2h_bytes_per_step": bytes_state, "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks,
+            "mixed": mixed,
+            "time_to_tol": ttt,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
