@@ -221,6 +221,27 @@ nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, double Kn, const
                                   const double *dev_coeffs, double *dev_R_out, double *norm_out,
                                   void *cuda_stream);
 
+/* Batches (BASELINE's batched form; the paper solves one cavity at a time).  A batch runs
+ * the V-cycles of several contexts in lockstep, aligned by depth below each context's finest
+ * level: every FS stage of all problems (pre-smoothing at one depth together with the
+ * coarsest solves reached there, or post-smoothing at one depth) is ONE persistent launch
+ * whose work queue merges the problems' exact-order schedules by earliest start, so small
+ * problems share the GPU.  Contexts must have the same M, order, slope, s1, s2, s3, model,
+ * gamma = 1 and precision 0; grids, Kn and walls may differ.  All batch work is issued on
+ * the first context's stream.  The caller owns the batch workspace (>= 256-byte aligned,
+ * size from nrmg_batch_workspace_bytes, 0 when the contexts are incompatible); the batch
+ * keeps pointers to the contexts, which must outlive it.  Per-problem results follow
+ * nrmg_fas_cycle / nrmg_solve (arrays of n entries); a problem's cycle count is the cycle at
+ * which it first reached tol; nrmg_batch_solve keeps cycling until every problem has. */
+typedef struct nrmg_batch nrmg_batch;
+size_t nrmg_batch_workspace_bytes(nrmg_ctx *const *ctxs, int n);
+nrmg_status nrmg_batch_create(nrmg_ctx *const *ctxs, int n, void *dev_workspace, size_t ws_bytes,
+                              nrmg_batch **out);
+nrmg_status nrmg_batch_destroy(nrmg_batch *batch);
+nrmg_status nrmg_batch_fas_cycle(nrmg_batch *batch, double *rel_res_out);
+nrmg_status nrmg_batch_solve(nrmg_batch *batch, double tol, int max_cycles, int *cycles_out, double *rel_res_out);
+long long nrmg_batch_launch_count(const nrmg_batch *batch);
+
 /* Human-readable name of a status, and the last error message of a context
  * (a static empty string when there is none; ctx may be NULL). */
 const char *nrmg_status_str(nrmg_status s);

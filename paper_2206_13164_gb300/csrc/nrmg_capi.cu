@@ -255,11 +255,21 @@ void sweep_order(int nx, int ny, int k, int *o) {
 // order is topological, so CTAs taking items in this order never wait on an item not yet
 // taken, and items of consecutive sweeps and steps interleave as early as the serial order
 // allows.
+void asap_schedule_keys(int nx, int ny, int reach, int steps, std::vector<std::pair<int, int>> &keys);
+
 void asap_schedule(int nx, int ny, int reach, int steps, std::vector<int> &queue) {
+  std::vector<std::pair<int, int>> keys;
+  asap_schedule_keys(nx, ny, reach, steps, keys);
+  queue.resize(keys.size());
+  for (size_t q = 0; q < keys.size(); ++q) queue[q] = keys[q].second;
+}
+
+// (start time, item) of every item of FS^steps, sorted by start time (see asap_schedule)
+void asap_schedule_keys(int nx, int ny, int reach, int steps, std::vector<std::pair<int, int>> &keys) {
   const int nc = nx * ny, V = 4 * steps;
   std::vector<int> tv((size_t)(V + 1) * nc, 0);
   std::vector<int> ord(nc);
-  std::vector<std::pair<int, int>> keys;
+  keys.clear();
   keys.reserve((size_t)V * nc);
   const int di[8] = {1, -1, 0, 0, 2, -2, 0, 0}, dj[8] = {0, 0, 1, -1, 0, 0, 2, -2};
   const int nnb = reach == 2 ? 8 : 4;
@@ -284,8 +294,6 @@ void asap_schedule(int nx, int ny, int reach, int steps, std::vector<int> &queue
     }
   std::stable_sort(keys.begin(), keys.end(),
                    [](const std::pair<int, int> &a, const std::pair<int, int> &b) { return a.first < b.first; });
-  queue.resize(keys.size());
-  for (size_t q = 0; q < keys.size(); ++q) queue[q] = keys[q].second;
 }
 
 // ------------------------------------------------------------------ workspace layout
@@ -980,6 +988,300 @@ const char *nrmg_status_str(nrmg_status s) {
 }
 
 const char *nrmg_last_error(const nrmg_ctx *ctx) { return ctx ? ctx->err : ""; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches of problems
+// A batch runs the V-cycles of several problems in lockstep, aligned by depth below each
+// problem's finest level.  Every FS stage (the pre-smoothing at one depth, the coarsest
+// solves reached at that depth, the post-smoothing at one depth) of all problems is one
+// persistent launch whose queue merges the problems' dependency-graph schedules by start time.
+struct nrmg_batch {
+  std::vector<nrmg_ctx *> ctx;
+  cudaStream_t stream;
+  struct Stage {
+    int ndesc;
+    BatchDesc *desc;        // device
+    int2 *items;            // device
+    long long nitems;
+    std::vector<std::pair<int, int>> ver;  // (problem, level) whose counters are reset
+  };
+  std::vector<Stage> down, up;  // down[d]: depth d pre-smoothing / coarsest; up[d]: depth d post
+  int *ctl;                     // device: [0] item counter, [1] abort word
+  int grid;
+  int depth;
+  long long launches;
+  char err[256];
+};
+
+namespace {
+
+bool batch_compatible(nrmg_ctx *const *c, int n) {
+  if (!c || n < 1) return false;
+  for (int b = 0; b < n; ++b) {
+    if (!c[b]) return false;
+    const nrmg_opts &o = c[b]->opts, &o0 = c[0]->opts;
+    if (c[b]->M != c[0]->M || o.order != o0.order || o.slope != o0.slope || o.s1 != o0.s1 || o.s2 != o0.s2 ||
+        o.s3 != o0.s3 || o.gamma != 1 || o.precision != 0 || c[b]->coll.model != c[0]->coll.model)
+      return false;
+  }
+  return true;
+}
+
+// the FS stages of a batched V-cycle; ws == nullptr only sizes them
+size_t batch_stages(nrmg_ctx *const *c, int n, char *ws, nrmg_batch *B) {
+  int D = 0;
+  for (int b = 0; b < n; ++b) D = std::max(D, c[b]->levels - 1);
+  size_t off = 256;  // control words first
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    size_t o = off;
+    off += bytes;
+    return o;
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int d = (pass == 0 ? 0 : D - 1); pass == 0 ? d <= D : d >= 0; d += (pass == 0 ? 1 : -1)) {
+      // entries of this stage: (problem, level, steps)
+      std::vector<int> eb, el, es;
+      for (int b = 0; b < n; ++b) {
+        int l = c[b]->levels - 1 - d;
+        if (pass == 0 && l >= 0) {
+          eb.push_back(b);
+          el.push_back(l);
+          es.push_back(l == 0 ? c[b]->opts.s3 : c[b]->opts.s1);
+        } else if (pass == 1 && l >= 1) {
+          eb.push_back(b);
+          el.push_back(l);
+          es.push_back(c[b]->opts.s2);
+        }
+      }
+      long long nit = 0;
+      for (size_t e = 0; e < eb.size(); ++e) nit += (long long)es[e] * 4 * c[eb[e]]->lev[el[e]].ncell;
+      size_t od = take(sizeof(BatchDesc) * eb.size()), oi = take(sizeof(int2) * (size_t)nit);
+      if (!ws) continue;
+      nrmg_batch::Stage S;
+      S.ndesc = (int)eb.size();
+      S.desc = (BatchDesc *)(ws + od);
+      S.items = (int2 *)(ws + oi);
+      S.nitems = nit;
+      std::vector<BatchDesc> hd(eb.size());
+      std::vector<std::pair<long long, int2>> all;
+      all.reserve(nit);
+      for (size_t e = 0; e < eb.size(); ++e) {
+        nrmg_ctx *x = c[eb[e]];
+        hd[e].K = x->K;
+        hd[e].K.abort_flag = B->ctl + 1;
+        hd[e].L = x->lev[el[e]];
+        hd[e].L.has_r = el[e] < x->levels - 1 ? 1 : 0;
+        S.ver.push_back({eb[e], el[e]});
+        std::vector<std::pair<int, int>> keys;
+        asap_schedule_keys(hd[e].L.nx, hd[e].L.ny, x->K.reach, es[e], keys);
+        for (auto &kv : keys) all.push_back({(long long)kv.first, make_int2((int)e, kv.second)});
+      }
+      std::stable_sort(all.begin(), all.end(),
+                       [](const std::pair<long long, int2> &a, const std::pair<long long, int2> &b) {
+                         return a.first < b.first;
+                       });
+      std::vector<int2> hi(all.size());
+      for (size_t q = 0; q < all.size(); ++q) hi[q] = all[q].second;
+      cudaMemcpyAsync(S.desc, hd.data(), sizeof(BatchDesc) * hd.size(), cudaMemcpyHostToDevice, B->stream);
+      cudaMemcpyAsync(S.items, hi.data(), sizeof(int2) * hi.size(), cudaMemcpyHostToDevice, B->stream);
+      cudaStreamSynchronize(B->stream);
+      (pass == 0 ? B->down : B->up).push_back(S);
+    }
+  }
+  return off + 256;
+}
+
+nrmg_status batch_fs(nrmg_batch *B, nrmg_batch::Stage &S) {
+  nrmg_ctx *ctx = B->ctx[0];  // for CK's error message
+  if (S.nitems == 0) return NRMG_OK;
+  for (auto &bl : S.ver) {
+    LevelDev &L = B->ctx[bl.first]->lev[bl.second];
+    CK(cudaMemsetAsync(L.ver, 0, sizeof(int) * L.ncell, B->stream));
+  }
+  CK(cudaMemsetAsync(B->ctl, 0, sizeof(int), B->stream));
+  long long g = std::min<long long>(B->grid, S.nitems);
+  Consts K0 = B->ctx[0]->K;  // layout and tables (same M for the whole batch), batch abort word
+  K0.abort_flag = B->ctl + 1;
+  CK(launch_fs_batch(S.desc, S.items, S.nitems, B->ctl, K0, (int)g, B->stream));
+  B->launches += 1;
+  return NRMG_OK;
+}
+
+// one batched V-cycle with mass correction; the norms are left in each context's dscal[0]
+nrmg_status batch_cycle_async(nrmg_batch *B) {
+  const int n = (int)B->ctx.size();
+  nrmg_status s;
+  // work of the contexts goes to the batch stream
+  std::vector<cudaStream_t> saved(n);
+  for (int b = 0; b < n; ++b) {
+    saved[b] = B->ctx[b]->stream;
+    B->ctx[b]->stream = B->stream;
+    B->ctx[b]->lev[B->ctx[b]->levels - 1].has_r = 0;
+  }
+  auto restore = [&]() {
+    for (int b = 0; b < n; ++b) B->ctx[b]->stream = saved[b];
+  };
+  for (int d = 0; d <= B->depth; ++d) {
+    if ((s = batch_fs(B, B->down[d])) != NRMG_OK) return restore(), s;
+    for (int b = 0; b < n; ++b) {
+      int l = B->ctx[b]->levels - 1 - d;
+      if (l >= 1 && (s = two_grid_setup(B->ctx[b], l)) != NRMG_OK) return restore(), s;
+    }
+  }
+  for (int d = B->depth - 1, u = 0; d >= 0; --d, ++u) {
+    for (int b = 0; b < n; ++b) {
+      int l = B->ctx[b]->levels - 1 - d;
+      if (l >= 1 && (s = two_grid_update(B->ctx[b], l)) != NRMG_OK) return restore(), s;
+    }
+    if ((s = batch_fs(B, B->up[u])) != NRMG_OK) return restore(), s;
+  }
+  for (int b = 0; b < n; ++b) {
+    nrmg_ctx *ctx = B->ctx[b];
+    if ((s = mass_correct(ctx)) != NRMG_OK) return restore(), s;
+    int g = 0;
+    if ((s = residual(ctx, ctx->levels - 1, kResOut, nullptr, ctx->N, &g)) != NRMG_OK) return restore(), s;
+    cudaError_t e = launch_reduce_norm(ctx->partials, g, 1.0 / (ctx->grid.lx * ctx->grid.ly), ctx->dscal, B->stream);
+    if (e != cudaSuccess) return restore(), NRMG_ERR_CUDA;
+    ctx->launches += 1;
+  }
+  restore();
+  return NRMG_OK;
+}
+
+nrmg_status batch_norms(nrmg_batch *B, std::vector<double> &out) {
+  const int n = (int)B->ctx.size();
+  out.assign(n, 0.0);
+  std::vector<int> st(n, 0);
+  for (int b = 0; b < n; ++b) {
+    if (cudaMemcpyAsync(&out[b], B->ctx[b]->dscal, sizeof(double), cudaMemcpyDeviceToHost, B->stream) != cudaSuccess)
+      return NRMG_ERR_CUDA;
+    if (cudaMemcpyAsync(&st[b], B->ctx[b]->dstatus, sizeof(int), cudaMemcpyDeviceToHost, B->stream) != cudaSuccess)
+      return NRMG_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return NRMG_ERR_CUDA;
+  for (int b = 0; b < n; ++b)
+    if (st[b] != 0) {
+      cudaMemsetAsync(B->ctx[b]->dstatus, 0, 2 * sizeof(int), B->stream);
+      cudaMemsetAsync(B->ctl, 0, 2 * sizeof(int), B->stream);
+      cudaStreamSynchronize(B->stream);
+      snprintf(B->err, sizeof(B->err), "problem %d reported status %d", b, st[b]);
+      return (nrmg_status)st[b];
+    }
+  return NRMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t nrmg_batch_workspace_bytes(nrmg_ctx *const *ctxs, int n) {
+  if (!batch_compatible(ctxs, n)) return 0;
+  return batch_stages(ctxs, n, nullptr, nullptr);
+}
+
+nrmg_status nrmg_batch_create(nrmg_ctx *const *ctxs, int n, void *dev_workspace, size_t ws_bytes,
+                              nrmg_batch **out) {
+  if (!out) return NRMG_ERR_ARG;
+  *out = nullptr;
+  if (!batch_compatible(ctxs, n) || !dev_workspace || ((uintptr_t)dev_workspace & 255)) return NRMG_ERR_ARG;
+  size_t need = nrmg_batch_workspace_bytes(ctxs, n);
+  if (ws_bytes < need) return NRMG_ERR_OOM;
+  nrmg_batch *B = new nrmg_batch();
+  B->ctx.assign(ctxs, ctxs + n);
+  B->stream = ctxs[0]->stream;
+  B->ctl = (int *)dev_workspace;
+  B->launches = 0;
+  B->err[0] = 0;
+  int D = 0;
+  for (int b = 0; b < n; ++b) D = std::max(D, ctxs[b]->levels - 1);
+  B->depth = D;
+  B->grid = ctxs[0]->nsm * std::max(1, ctxs[0]->occ[0]);
+  if (cudaMemsetAsync(B->ctl, 0, 256, B->stream) != cudaSuccess) {
+    delete B;
+    return NRMG_ERR_CUDA;
+  }
+  batch_stages(ctxs, n, (char *)dev_workspace, B);
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) {
+    delete B;
+    return NRMG_ERR_CUDA;
+  }
+  *out = B;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_batch_destroy(nrmg_batch *B) {
+  if (!B) return NRMG_ERR_ARG;
+  cudaStreamSynchronize(B->stream);
+  delete B;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_batch_fas_cycle(nrmg_batch *B, double *rel_res_out) {
+  if (!B) return NRMG_ERR_ARG;
+  const int n = (int)B->ctx.size();
+  nrmg_status s;
+  std::vector<double> nr;
+  // reference residuals of the problems that have none yet
+  for (int b = 0; b < n; ++b) {
+    nrmg_ctx *ctx = B->ctx[b];
+    if (!ctx->have_res0) {
+      ctx->lev[ctx->levels - 1].has_r = 0;
+      if ((s = norm_of(ctx, ctx->levels - 1, nullptr, &ctx->res0)) != NRMG_OK) return s;
+      ctx->have_res0 = 1;
+    }
+  }
+  if ((s = batch_cycle_async(B)) != NRMG_OK) return s;
+  if ((s = batch_norms(B, nr)) != NRMG_OK) return s;
+  if (rel_res_out)
+    for (int b = 0; b < n; ++b) rel_res_out[b] = B->ctx[b]->res0 > 0.0 ? nr[b] / B->ctx[b]->res0 : 0.0;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_batch_solve(nrmg_batch *B, double tol, int max_cycles, int *cycles_out, double *rel_res_out) {
+  if (!B || !(tol >= 0.0) || max_cycles < 0) return NRMG_ERR_ARG;
+  const int n = (int)B->ctx.size();
+  std::vector<double> rel(n, 1.0);
+  std::vector<int> cyc(n, 0);
+  nrmg_status s = NRMG_OK;
+  for (int b = 0; b < n; ++b) {
+    nrmg_ctx *ctx = B->ctx[b];
+    ctx->lev[ctx->levels - 1].has_r = 0;
+    if ((s = norm_of(ctx, ctx->levels - 1, nullptr, &ctx->res0)) != NRMG_OK) return s;
+    ctx->have_res0 = 1;
+    rel[b] = ctx->res0 > 0.0 ? 1.0 : 0.0;
+  }
+  auto done = [&]() {
+    for (int b = 0; b < n; ++b)
+      if (rel[b] > tol) return false;
+    return true;
+  };
+  int it = 0;
+  while (!done() && it < max_cycles) {
+    std::vector<double> r(n);
+    if ((s = nrmg_batch_fas_cycle(B, r.data())) != NRMG_OK) break;
+    ++it;
+    for (int b = 0; b < n; ++b)
+      if (rel[b] > tol) {
+        rel[b] = r[b];
+        cyc[b] = it;
+      }
+  }
+  if (cycles_out)
+    for (int b = 0; b < n; ++b) cycles_out[b] = cyc[b];
+  if (rel_res_out)
+    for (int b = 0; b < n; ++b) rel_res_out[b] = rel[b];
+  if (s == NRMG_OK && !done()) s = NRMG_ERR_NOT_CONVERGED;
+  return s;
+}
+
+long long nrmg_batch_launch_count(const nrmg_batch *B) {
+  if (!B) return 0;
+  long long n = B->launches;
+  for (nrmg_ctx *c : B->ctx) n += c->launches;
+  return n;
+}
 
 }  // extern "C"
 

@@ -67,6 +67,12 @@ __host__ __device__ inline int nmom_even(int M) {
   return n;
 }
 
+// One problem of a batched FS launch: its scheme constants and the level being swept.
+struct BatchDesc {
+  Consts K;
+  LevelDev L;
+};
+
 // Size in bytes of the dynamic shared memory of the cell kernels.
 size_t cell_smem_bytes(int M, int NP);
 
@@ -74,6 +80,9 @@ size_t cell_smem_bytes(int M, int NP);
 // FS^steps on level L.  queue (may be NULL): the order in which the persistent CTAs take the
 // steps*4*ncell items, each item (s*4 + k)*ncell + c; NULL = sweep by sweep in anti-diagonal order.
 cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, const int *queue, int grid, cudaStream_t st);
+// FS sweeps of several problems in one persistent launch (items: problem, level-queue item).
+cudaError_t launch_fs_batch(const BatchDesc *desc, const int2 *items, long long total, int *counter,
+                            const Consts &K0, int grid, cudaStream_t st);
 cudaError_t launch_residual(const Consts &K, const LevelDev &L, int mode, double *out, int out_stride,
                             double *partials, int grid, cudaStream_t st);
 cudaError_t launch_restrict(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st);

@@ -314,12 +314,67 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v) {
 }
 
 // ------------------------------------------------------------------ FS^steps (Algorithm 1)
+// One sweep item: update cell c (i,j) of sweep k to version v once the cross stencil holds
+// the versions of the serial order (the newest for a neighbour that sweep Dk visits earlier,
+// the previous one otherwise), then publish v.  Returns false when the launch must stop.
+__device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c, int k, int v) {
+  const int tid = threadIdx.x, NP = K.NP;
+  const int i = c % L.nx, j = c / L.nx;
+  if (tid < 9) {
+    int di = c_nb_di[tid], dj = c_nb_dj[tid];
+    int ii = i + di, jj = j + dj;
+    int reach = abs(di) + abs(dj);
+    if (ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && reach <= K.reach) {
+      // sweep Dk: i ascending for D1, D4; j ascending for D1, D2 (outer loop i, inner j)
+      int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
+      bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
+      int need = (tid != 0 && before) ? v : v - 1;
+      const int *flag = L.ver + (size_t)jj * L.nx + ii;
+      if (ld_acquire(flag) < need) {
+        unsigned long long t0 = gtimer();
+        while (ld_acquire(flag) < need) {
+          if (ld_volatile(K.abort_flag)) break;
+          if (gtimer() - t0 > kWaitLimitNs) {
+            raise_status(K, kStTimeout, true);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) s.iarr[I_ABORT] = ld_volatile(K.abort_flag);
+  __syncthreads();
+  if (s.iarr[I_ABORT]) return false;
+  // ---- R_ij(f) - r_ij, then f + dt (R - r) into VA slot 4, back to Grad form
+  cell_residual<true>(K, L, s, i, j,
+                      [&](int o, double Rr) { s.VA[4 * NP + o] = fma(s.sc[S_DT], Rr, s.cst[4 + o]); });
+  __syncthreads();
+  double pcell[4];
+  for (int e = 0; e < 4; ++e) pcell[e] = s.cst[e];
+  bool ok = regrad(K, s, pcell, 4);
+  double *Fo = L.F + (size_t)c * NP;
+  for (int q = tid; q < K.NE; q += kThreads) {
+    const int o = s.eidx[q];
+    Fo[o] = s.VB[4 * NP + o];
+  }
+  if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+  if (!ok && tid == 0) raise_status(K, kStNonPhysical, true);
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_release(L.ver + c, v);
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int steps, const int *queue) {
   extern __shared__ __align__(16) char smem_raw[];
   Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
   load_tables(K, s);
   __syncthreads();
-  const int tid = threadIdx.x, N = K.N, NP = K.NP;
+  const int tid = threadIdx.x;
   const int ncell = L.ncell;
   const long long total = (long long)steps * 4 * ncell;
   for (;;) {
@@ -342,55 +397,42 @@ __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int 
       k = (int)((item / ncell) % 4);
       c = L.order[(size_t)k * ncell + (int)(item % ncell)];
     }
-    const int i = c % L.nx, j = c / L.nx;
-    const int v = 4 * st + k + 1;  // the version this update produces
-    // ---- wait until the cross stencil holds the versions of the serial order
-    if (tid < 9) {
-      int di = c_nb_di[tid], dj = c_nb_dj[tid];
-      int ii = i + di, jj = j + dj;
-      int reach = abs(di) + abs(dj);
-      if (ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && reach <= K.reach) {
-        // sweep Dk: i ascending for D1, D4; j ascending for D1, D2 (outer loop i, inner j)
-        int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
-        bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
-        int need = (tid != 0 && before) ? v : v - 1;
-        const int *flag = L.ver + (size_t)jj * L.nx + ii;
-        if (ld_acquire(flag) < need) {
-          unsigned long long t0 = gtimer();
-          while (ld_acquire(flag) < need) {
-            if (ld_volatile(K.abort_flag)) break;
-            if (gtimer() - t0 > kWaitLimitNs) {
-              raise_status(K, kStTimeout, true);
-              break;
-            }
-            __nanosleep(32);
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (tid == 0) s.iarr[I_ABORT] = ld_volatile(K.abort_flag);
-    __syncthreads();
-    if (s.iarr[I_ABORT]) break;
-    // ---- R_ij(f) - r_ij, then f + dt (R - r) into VA slot 0
-    cell_residual<true>(K, L, s, i, j,
-                        [&](int o, double Rr) { s.VA[4 * NP + o] = fma(s.sc[S_DT], Rr, s.cst[4 + o]); });
-    __syncthreads();
-    double pcell[4];
-    for (int e = 0; e < 4; ++e) pcell[e] = s.cst[e];
-    bool ok = regrad(K, s, pcell, 4);
-    double *Fo = L.F + (size_t)c * NP;
-    for (int q = tid; q < K.NE; q += kThreads) {
-      const int o = s.eidx[q];
-      Fo[o] = s.VB[4 * NP + o];
-    }
-    if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
-    if (!ok && tid == 0) raise_status(K, kStNonPhysical, true);
-    __syncthreads();
+    if (!fs_item(K, L, s, c, k, 4 * st + k + 1)) break;
+  }
+}
+
+// FS sweeps of several problems (same M and scheme) in one persistent launch.  items[q] =
+// (problem, item of that problem's level queue); the problem descriptors (scheme constants
+// and level) are copied into shared memory per item.  All descriptors share one abort word.
+__global__ void __launch_bounds__(kThreads) fs_batch_kernel(const BatchDesc *desc, const int2 *items,
+                                                            long long total, int *counter, Consts K0) {
+  extern __shared__ __align__(16) char smem_raw[];
+  __shared__ BatchDesc bd;
+  Sm s = bind_smem(smem_raw, K0.M, K0.N, K0.NP);
+  load_tables(K0, s);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  int cur = -1;
+  for (;;) {
     if (tid == 0) {
-      __threadfence();
-      st_release(L.ver + c, v);
+      int it = atomicAdd(counter, 1);
+      if (ld_volatile(K0.abort_flag)) it = (int)total;
+      s.iarr[I_ITEM] = it;
     }
+    __syncthreads();
+    const long long item = s.iarr[I_ITEM];
+    if (item >= total) break;
+    const int2 iv = items[item];
+    if (iv.x != cur) {  // uniform: every thread read the same item
+      const int *src = (const int *)(desc + iv.x);
+      int *dst = (int *)&bd;
+      for (int w = tid; w < (int)(sizeof(BatchDesc) / sizeof(int)); w += kThreads) dst[w] = src[w];
+      cur = iv.x;
+      __syncthreads();
+    }
+    const int ncell = bd.L.ncell, qv = iv.y;
+    const int st = qv / (4 * ncell), k = (qv / ncell) % 4, c = qv % ncell;
+    if (!fs_item(bd.K, bd.L, s, c, k, 4 * st + k + 1)) break;
   }
 }
 
@@ -666,6 +708,23 @@ static size_t smem_for(const Consts &K) { return make_layout(K.M, K.N, K.NP).tot
 cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, const int *queue, int grid, cudaStream_t st) {
   ensure_smem_attr(fs_kernel);
   fs_kernel<<<grid, kThreads, smem_for(K), st>>>(K, L, steps, queue);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fs_batch(const BatchDesc *desc, const int2 *items, long long total, int *counter,
+                            const Consts &K0, int grid, cudaStream_t st) {
+  static bool done = false;
+  if (!done) {
+    // the descriptor copy is static shared memory: the dynamic part gets the rest
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fs_batch_kernel);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fs_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024 - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  fs_batch_kernel<<<grid, kThreads, smem_for(K0), st>>>(desc, items, total, counter, K0);
   return cudaGetLastError();
 }
 

@@ -95,6 +95,18 @@ def lib():
         L.nrmg_fs_profile_levels.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong)]
         L.nrmg_peak_fma.restype = c_int
         L.nrmg_peak_fma.argtypes = [c_int, c_int, c_void_p, POINTER(c_double)]
+        L.nrmg_batch_workspace_bytes.restype = c_size_t
+        L.nrmg_batch_workspace_bytes.argtypes = [POINTER(c_void_p), c_int]
+        L.nrmg_batch_create.restype = c_int
+        L.nrmg_batch_create.argtypes = [POINTER(c_void_p), c_int, c_void_p, c_size_t, POINTER(c_void_p)]
+        L.nrmg_batch_destroy.restype = c_int
+        L.nrmg_batch_destroy.argtypes = [c_void_p]
+        L.nrmg_batch_fas_cycle.restype = c_int
+        L.nrmg_batch_fas_cycle.argtypes = [c_void_p, POINTER(c_double)]
+        L.nrmg_batch_solve.restype = c_int
+        L.nrmg_batch_solve.argtypes = [c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]
+        L.nrmg_batch_launch_count.restype = c_longlong
+        L.nrmg_batch_launch_count.argtypes = [c_void_p]
         L.nrmg_status_str.restype = ctypes.c_char_p
         L.nrmg_status_str.argtypes = [c_int]
         L.nrmg_last_error.restype = ctypes.c_char_p
@@ -267,6 +279,57 @@ def peak_fma(precision: int = 0, iters: int = 4096, stream=None) -> float:
     if st != 0:
         raise RuntimeError(f"nrmg_peak_fma failed ({st})")
     return out.value
+
+
+class Batch:
+    """Several Solvers (same M and scheme; grids, Kn, walls may differ) cycled in lockstep with
+    one persistent FS launch per stage.  All work runs on the first solver's stream."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.L = lib()
+        n = len(self.solvers)
+        self._arr = (c_void_p * n)(*[s.ctx.value for s in self.solvers])
+        nbytes = self.L.nrmg_batch_workspace_bytes(self._arr, n)
+        if nbytes == 0:
+            raise NrmgError(ERR_ARG, "nrmg_batch_workspace_bytes", "incompatible solvers")
+        dev = self.solvers[0].device
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.h = c_void_p()
+        st = self.L.nrmg_batch_create(self._arr, n, c_void_p(self.workspace.data_ptr()), nbytes, ctypes.byref(self.h))
+        if st != OK:
+            raise NrmgError(st, "nrmg_batch_create")
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.nrmg_batch_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fas_cycle(self):
+        n = len(self.solvers)
+        rel = (c_double * n)()
+        st = self.L.nrmg_batch_fas_cycle(self.h, rel)
+        if st != OK:
+            raise NrmgError(st, "nrmg_batch_fas_cycle", self.L.nrmg_last_error(self.solvers[0].ctx).decode())
+        return list(rel)
+
+    def solve(self, tol=1e-8, max_cycles=200):
+        n = len(self.solvers)
+        cyc, rel = (c_int * n)(), (c_double * n)()
+        st = self.L.nrmg_batch_solve(self.h, tol, max_cycles, cyc, rel)
+        if st not in (OK, ERR_NOT_CONVERGED):
+            raise NrmgError(st, "nrmg_batch_solve")
+        return st, list(cyc), list(rel)
+
+    @property
+    def launches(self) -> int:
+        return int(self.L.nrmg_batch_launch_count(self.h))
 
 
 def from_problem(prob, **kw) -> Solver:

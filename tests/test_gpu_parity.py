@@ -282,3 +282,46 @@ def test_mixed_precision_reaches_the_fp64_solution(name, prob):
     # the residual the mixed form stops on is the FP64 residual of the same operator
     _, n_final = G.residual()
     assert n_final <= 1.0000001e-8 * O.res0()
+
+
+# ------------------------------------------------------------------ batches (one persistent launch per stage)
+def _batch_problems():
+    return [lid_cavity(32, 5, 0.1, 0.3, order=2, slope=2, levels=3),
+            lid_cavity(16, 5, 0.5, 0.1, order=2, slope=2, levels=2),
+            lid_cavity(64, 5, 0.05, 0.2, order=2, slope=2, levels=4).replace(ny=32),
+            heated_cavity(16, 5, 0.3, order=2, slope=2, levels=2, model=BGK)]
+
+
+def test_batch_cycles_equal_individual_cycles():
+    """A batched cycle performs each problem's V-cycle operations in the same order as
+    nrmg_fas_cycle; states agree with solving the problems one by one up to the compiler's
+    different FMA contraction in the two launch paths (a few ulps)."""
+    probs = _batch_problems()
+    single = [gpu(p) for p in probs]
+    batched = [gpu(p) for p in probs]
+    B = nrmg.Batch(batched)
+    for _ in range(2):
+        rb = B.fas_cycle()
+        rs = [S.fas_cycle() for S in single]
+        assert np.allclose(rb, rs, rtol=1e-12, atol=0)
+    for Sg, Sb in zip(single, batched):
+        Pg, Fg = Sg.get_state()
+        Pb, Fb = Sb.get_state()
+        assert_close(N(Pb), N(Pg), 1e-13, "params")
+        assert_close(N(Fb), N(Fg), 1e-13, "coeffs")
+
+
+def test_batch_solve_matches_oracle():
+    probs = _batch_problems()[:2]
+    batched = [gpu(p) for p in probs]
+    B = nrmg.Batch(batched)
+    st, cyc, rel = B.solve(1e-8, 200)
+    assert st == 0 and max(rel) <= 1e-8
+    total = max(cyc)  # the batch keeps cycling every problem until the last one converged
+    for p, S, c in zip(probs, batched, cyc):
+        O = oracle_solver(p)
+        sto, co, ro = O.solve(1e-8, 200)
+        assert sto == 0 and co == c
+        for _ in range(total - co):
+            O.fas_cycle()
+        compare_fields(N(S.fields()), O.fields(), 1e-10)
