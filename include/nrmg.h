@@ -104,6 +104,8 @@ typedef struct {
   double cfl;
   int s1, s2, s3, gamma;
   int precision;
+  double dtnu; /* > 0: local time step capped at dtnu / nu, the collision frequency (0 = the
+                  CFL step of eq. local-CFL alone); changes the iteration, not its fixed point */
 } nrmg_opts;
 
 /* Bytes of device workspace nrmg_create needs; 0 when the arguments are invalid. */
@@ -241,6 +243,9 @@ nrmg_status nrmg_batch_destroy(nrmg_batch *batch);
 nrmg_status nrmg_batch_fas_cycle(nrmg_batch *batch, double *rel_res_out);
 nrmg_status nrmg_batch_solve(nrmg_batch *batch, double tol, int max_cycles, int *cycles_out, double *rel_res_out);
 long long nrmg_batch_launch_count(const nrmg_batch *batch);
+/* Persistent CTAs per SM of the batched FS launches (1 .. the kernel's occupancy; default the
+ * occupancy): the knob the batch autotuner sweeps. */
+nrmg_status nrmg_batch_set_grid(nrmg_batch *batch, int ctas_per_sm);
 
 /* Human-readable name of a status, and the last error message of a context
  * (a static empty string when there is none; ctx may be NULL). */

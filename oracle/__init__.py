@@ -45,6 +45,7 @@ class OrConfig(ctypes.Structure):
         ("beta", c_double), ("order", c_int), ("slope", c_int), ("cfl", c_double),
         ("s1", c_int), ("s2", c_int), ("s3", c_int), ("gamma", c_int),
         ("wall_u", (c_double * 3) * 4), ("wall_theta", c_double * 4), ("wall_chi", c_double * 4),
+        ("dtnu", c_double),
     ]
 
 

@@ -307,6 +307,7 @@ typedef struct {
   double wall_u[4][3]; /* walls: 0 bottom y=0, 1 right x=lx, 2 top y=ly, 3 left x=0 */
   double wall_theta[4];
   double wall_chi[4];
+  double dtnu; /* > 0: local time step capped at dtnu / nu (0: the CFL step alone) */
 } or_config;
 
 typedef struct {
@@ -686,6 +687,9 @@ static int regrad(const or_solver *S, const double *p, const double *g, double *
 /* ------------------------------------------------------------------ */
 /* One Gauss-Seidel cell update of Algorithm 1:                        */
 /*   dt from eq. (local-CFL) with the current state, CFL number cfl;   */
+/*   optionally capped at dtnu / nu (reading for small Kn, where the    */
+/*   explicit collision step nu dt would exceed its stability bound;    */
+/*   the cap changes the iteration, not its fixed point);               */
 /*   f <- f + dt (R_ij(f) - r_ij), then back to Grad form.             */
 /* ------------------------------------------------------------------ */
 static int cell_update(or_solver *S, or_level *L, int i, int j) {
@@ -694,6 +698,10 @@ static int cell_update(or_solver *S, or_level *L, int i, int j) {
   double R[OR_MAXN], r[OR_MAXN], g[OR_MAXN], pn[4], fn[OR_MAXN];
   double sq = sqrt(pc[3]);
   double dt = S->c.cfl / ((fabs(pc[0]) + S->C * sq) / L->dx + (fabs(pc[1]) + S->C * sq) / L->dy);
+  if (S->c.dtnu > 0.0) {
+    double nu = S->c.beta * sqrt(M_PI / 2.0) * fc[0] * pow(pc[3], 1.0 - S->c.omega) / S->c.Kn;
+    dt = fmin(dt, S->c.dtnu / nu);
+  }
   cell_R(S, L, i, j, R);
   rhs_in(S, L, c, pc, r);
   for (int o = 0; o < n; ++o) g[o] = fc[o] + dt * (R[o] - r[o]);

@@ -453,6 +453,7 @@ bool opts_ok(const nrmg_opts *o) {
   if (!o) return false;
   if (o->order != 1 && o->order != 2) return false;
   if (o->slope < 0 || o->slope > 2) return false;
+  if (!(o->dtnu >= 0.0)) return false;
   if (!(o->cfl > 0.0) || o->s1 < 0 || o->s2 < 0 || o->s3 < 0 || o->gamma < 1 || o->gamma > 2) return false;
   if (o->precision != 0 && o->precision != 1) return false;
   return true;
@@ -719,6 +720,7 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
     K.omega = coll->omega;
     K.beta = coll->beta;
     K.cfl = opts->cfl;
+    K.dtnu = opts->dtnu;
     K.C = hermite_largest_root(M + 1);
     K.lx = grid->lx;
     K.ly = grid->ly;
@@ -1276,6 +1278,12 @@ nrmg_status nrmg_batch_solve(nrmg_batch *B, double tol, int max_cycles, int *cyc
   return s;
 }
 
+nrmg_status nrmg_batch_set_grid(nrmg_batch *B, int ctas_per_sm) {
+  if (!B || ctas_per_sm < 1 || ctas_per_sm > std::max(1, B->ctx[0]->occ[0])) return NRMG_ERR_ARG;
+  B->grid = B->ctx[0]->nsm * ctas_per_sm;
+  return NRMG_OK;
+}
+
 long long nrmg_batch_launch_count(const nrmg_batch *B) {
   if (!B) return 0;
   long long n = B->launches;
@@ -1371,6 +1379,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   K.omega = coll->omega;
   K.beta = coll->beta;
   K.cfl = opts->cfl;
+  K.dtnu = opts->dtnu;
   K.C = hermite_largest_root(M + 1);
   K.lx = grid->lx;
   K.ly = grid->ly;

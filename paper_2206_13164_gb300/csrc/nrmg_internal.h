@@ -43,6 +43,7 @@ struct Consts {
   int slope;   // 0 none, 1 central, 2 van Albada
   int model;
   double Kn, Pr, omega, beta, cfl, C;  // C = largest root of He_{M+1}
+  double dtnu;                         // > 0: time step capped at dtnu / nu
   double lx, ly;
   double wall_u[4][3], wall_theta[4];
   // tables (global memory, copied to shared memory by each CTA)

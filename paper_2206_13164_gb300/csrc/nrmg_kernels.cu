@@ -131,9 +131,12 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   if (tid == 32) {
     const double *f = pc + 4;
     double rho = f[0], th = pc[3];
-    s.sc[S_NU] = K.beta * sqrt(M_PI / 2.0) * rho * pow(th, 1.0 - K.omega) / K.Kn;
+    const double nu = K.beta * sqrt(M_PI / 2.0) * rho * pow(th, 1.0 - K.omega) / K.Kn;
+    s.sc[S_NU] = nu;
     double sq = sqrt(th);
-    s.sc[S_DT] = K.cfl / ((fabs(pc[0]) + K.C * sq) * L.idx + (fabs(pc[1]) + K.C * sq) * L.idy);
+    double dt = K.cfl / ((fabs(pc[0]) + K.C * sq) * L.idx + (fabs(pc[1]) + K.C * sq) * L.idy);
+    if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / nu);
+    s.sc[S_DT] = dt;
   }
   if (tid == 64) {
     double it = 1.0 / pc[3], t = 1.0;

@@ -82,8 +82,9 @@ __global__ void mixed_prep_kernel(Consts K, LevelDev L) {
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads) {
     const double *p = L.P + (size_t)c * 4;
     const double rho = L.F[(size_t)c * K.NP], th = p[3], sq = sqrt(th);
-    const double dt = K.cfl / ((fabs(p[0]) + K.C * sq) * L.idx + (fabs(p[1]) + K.C * sq) * L.idy);
     const double nu = K.beta * sqrt(M_PI / 2.0) * rho * pow(th, 1.0 - K.omega) / K.Kn;
+    double dt = K.cfl / ((fabs(p[0]) + K.C * sq) * L.idx + (fabs(p[1]) + K.C * sq) * L.idy);
+    if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / nu);
     float *a = L.aux32 + (size_t)c * 8;
     for (int e = 0; e < 4; ++e) a[e] = (float)p[e];
     a[4] = (float)dt;

@@ -38,7 +38,7 @@ class Collision(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("order", c_int), ("slope", c_int), ("cfl", c_double), ("s1", c_int), ("s2", c_int),
-                ("s3", c_int), ("gamma", c_int), ("precision", c_int)]
+                ("s3", c_int), ("gamma", c_int), ("precision", c_int), ("dtnu", c_double)]
 
 
 _lib = None
@@ -105,6 +105,8 @@ def lib():
         L.nrmg_batch_fas_cycle.argtypes = [c_void_p, POINTER(c_double)]
         L.nrmg_batch_solve.restype = c_int
         L.nrmg_batch_solve.argtypes = [c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]
+        L.nrmg_batch_set_grid.restype = c_int
+        L.nrmg_batch_set_grid.argtypes = [c_void_p, c_int]
         L.nrmg_batch_launch_count.restype = c_longlong
         L.nrmg_batch_launch_count.argtypes = [c_void_p]
         L.nrmg_status_str.restype = ctypes.c_char_p
@@ -142,8 +144,8 @@ class Solver:
     """
 
     def __init__(self, nx, ny, M, Kn, walls, levels=1, lx=1.0, ly=1.0, model=BGK, Pr=2.0 / 3.0, omega=0.81,
-                 beta=1.0, order=1, slope=0, cfl=0.9, s1=2, s2=2, s3=4, gamma=1, precision=0, device=None,
-                 stream=None):
+                 beta=1.0, order=1, slope=0, cfl=0.9, s1=2, s2=2, s3=4, gamma=1, precision=0, dtnu=0.0,
+                 device=None, stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("nrmg needs a CUDA device")
         self.L = lib()
@@ -151,7 +153,7 @@ class Solver:
         self.M, self.N, self.levels = M, nmom(M), levels
         self.nx, self.ny = nx, ny
         self.grid = Grid(nx, ny, lx, ly, levels)
-        self.opts = Opts(order, slope, cfl, s1, s2, s3, gamma, precision)
+        self.opts = Opts(order, slope, cfl, s1, s2, s3, gamma, precision, dtnu)
         self.coll = Collision(model, Pr, omega, beta)
         wa = (Wall * 4)()
         for k, (u, th, chi) in enumerate(walls):
@@ -331,13 +333,41 @@ class Batch:
     def launches(self) -> int:
         return int(self.L.nrmg_batch_launch_count(self.h))
 
+    def set_grid(self, ctas_per_sm: int):
+        st = self.L.nrmg_batch_set_grid(self.h, ctas_per_sm)
+        if st != OK:
+            raise NrmgError(st, "nrmg_batch_set_grid")
+
+    def autotune(self, candidates=(1, 2, 3), reps=1):
+        """Time one batched cycle per candidate CTAs/SM (the cycles advance the solution) and
+        keep the fastest.  Returns {candidate: seconds}."""
+        import time
+
+        times = {}
+        for c in candidates:
+            try:
+                self.set_grid(c)
+            except NrmgError:
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                self.fas_cycle()
+            torch.cuda.synchronize()
+            times[c] = (time.perf_counter() - t0) / reps
+        best = min(times, key=times.get)
+        self.set_grid(best)
+        self.tuned = best
+        return times
+
 
 def from_problem(prob, **kw) -> Solver:
     """Build a Solver from any object with the fields of a cavity problem description."""
     walls = [(tuple(w.u), w.theta, w.chi) for w in prob.walls]
     return Solver(prob.nx, prob.ny, prob.M, prob.Kn, walls, levels=prob.levels, lx=prob.lx, ly=prob.ly,
                   model=prob.model, Pr=prob.Pr, omega=prob.omega, beta=prob.beta, order=prob.order,
-                  slope=prob.slope, cfl=prob.cfl, s1=prob.s1, s2=prob.s2, s3=prob.s3, gamma=prob.gamma, **kw)
+                  slope=prob.slope, cfl=prob.cfl, s1=prob.s1, s2=prob.s2, s3=prob.s3, gamma=prob.gamma,
+                  dtnu=getattr(prob, "dtnu", 0.0), **kw)
 
 
 def residual_noalloc(prob, params, coeffs, want_R=True, stream=None):
@@ -353,7 +383,8 @@ def residual_noalloc(prob, params, coeffs, want_R=True, stream=None):
                                             c_void_p]
         L._noalloc_ready = True
     grid = Grid(prob.nx, prob.ny, prob.lx, prob.ly, prob.levels)
-    opts = Opts(prob.order, prob.slope, prob.cfl, prob.s1, prob.s2, prob.s3, prob.gamma, 0)
+    opts = Opts(prob.order, prob.slope, prob.cfl, prob.s1, prob.s2, prob.s3, prob.gamma, 0,
+                getattr(prob, "dtnu", 0.0))
     coll = Collision(prob.model, prob.Pr, prob.omega, prob.beta)
     wa = (Wall * 4)()
     for k, w in enumerate(prob.walls):

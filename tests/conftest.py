@@ -25,6 +25,7 @@ def oracle_config(prob):
     c.M, c.Kn, c.model, c.Pr, c.omega, c.beta = prob.M, prob.Kn, prob.model, prob.Pr, prob.omega, prob.beta
     c.order, c.slope, c.cfl = prob.order, prob.slope, prob.cfl
     c.s1, c.s2, c.s3, c.gamma = prob.s1, prob.s2, prob.s3, prob.gamma
+    c.dtnu = prob.dtnu
     for w in range(4):
         for d in range(3):
             c.wall_u[w][d] = prob.walls[w].u[d]

@@ -60,6 +60,7 @@ class Problem:
     s2: int = 2
     s3: int = 4
     gamma: int = 1
+    dtnu: float = 0.0  # > 0: local time step capped at dtnu / nu
 
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)

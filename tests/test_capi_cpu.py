@@ -37,7 +37,7 @@ def test_library_is_built_for_sm103a():
 
 
 def _args(nx=32, ny=32, levels=3, M=5, order=1, slope=0, precision=0):
-    return (nrmg.Grid(nx, ny, 1.0, 1.0, levels), M, nrmg.Opts(order, slope, 0.9, 2, 2, 4, 1, precision))
+    return (nrmg.Grid(nx, ny, 1.0, 1.0, levels), M, nrmg.Opts(order, slope, 0.9, 2, 2, 4, 1, precision, 0.0))
 
 
 def test_workspace_bytes_and_argument_checks():

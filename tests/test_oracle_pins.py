@@ -529,3 +529,40 @@ def test_multigrid_cycle_count_is_flat_fs_doubles():
     assert fs[16] > 1.5 * fs[8]
     assert cyc[16] <= 1.5 * cyc[8] + 2
     assert cyc[16] < fs[16] / 3
+
+
+def test_dt_cap_changes_the_step_not_the_fixed_point():
+    """With dtnu > 0 the local step is min(CFL step, dtnu/nu): the first cell of sweep D1 moves
+    by exactly that step, and the solved fields agree with the uncapped solve."""
+    M, N = 3, 8
+    base = lid_cavity(N, M, 0.02, 0.3, levels=1)
+    capped = base.replace(dtnu=0.5)
+    rng = np.random.default_rng(40)
+    P, F = random_state(rng, N, N, M)
+    S = oracle_solver(capped)
+    S.set_state(0, P, F)
+    R0 = S.cell_residual(0, 0, 0)
+    S.sweep(0, 1)
+    Pn, _ = S.get_state(0)
+    C = oracle.hermite_max_root(M + 1)
+    sq = math.sqrt(P[0, 3])
+    dt = 0.9 / ((abs(P[0, 0]) + C * sq) * N + (abs(P[0, 1]) + C * sq) * N)
+    nu = math.sqrt(math.pi / 2) * F[0, 0] * P[0, 3] ** 0.19 / 0.02
+    dt = min(dt, 0.5 / nu)
+    mac = oracle.macros(M, P[0], F[0] + dt * R0)
+    np.testing.assert_allclose(Pn[0], mac[1:], rtol=1e-13, atol=1e-15)
+    # at this Kn the explicit collision step of the uncapped sweep is unstable on 8x8 ...
+    S2 = oracle_solver(base.replace(s3=1))
+    st, c, rel = S2.solve(1e-10, 3000)
+    assert st == oracle.ERR_NONPHYSICAL
+    S3 = oracle_solver(capped.replace(s3=1))
+    st, c, rel = S3.solve(1e-10, 3000)
+    assert st == oracle.OK
+    # ... and where both are stable, both reach the same fixed point
+    fields = []
+    for cap in (0.0, 0.5):
+        S4 = oracle_solver(lid_cavity(N, M, 0.1, 0.3, levels=1, s3=1, dtnu=cap))
+        st, c, rel = S4.solve(1e-11, 3000)
+        assert st == 0
+        fields.append(S4.fields())
+    np.testing.assert_allclose(fields[0], fields[1], rtol=0, atol=1e-9)
