@@ -122,7 +122,8 @@ def run_batch64(args):
                                       "{64,128,256}, M in {5,8}, BGK, 2nd order; one batch per M, one persistent "
                                       "FS launch per stage", "step": "one batched V-cycle of all 64 instances",
                           "instances": {str(M): len(g) for M, g in groups.items()},
-                          "batch_build_s": t_build, "autotune_ctas_per_sm": {str(M): B.tuned for M, B in batches.items()},
+                          "batch_build_s": t_build,
+                          "graph_replay": {str(M): B.graph for M, B in batches.items()}, "autotune_ctas_per_sm": {str(M): B.tuned for M, B in batches.items()},
                           "autotune_s": {str(M): t for M, t in tune.items()}},
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)

@@ -246,6 +246,10 @@ long long nrmg_batch_launch_count(const nrmg_batch *batch);
 /* Persistent CTAs per SM of the batched FS launches (1 .. the kernel's occupancy; default the
  * occupancy): the knob the batch autotuner sweeps. */
 nrmg_status nrmg_batch_set_grid(nrmg_batch *batch, int ctas_per_sm);
+/* 1 when the batched cycle is replayed as a CUDA graph: the first nrmg_batch_fas_cycle runs
+ * eagerly, the second captures the cycle's launches (on a stream other than the legacy
+ * default stream) and every later one replays them; changing the grid captures again. */
+int nrmg_batch_graph(const nrmg_batch *batch);
 
 /* Human-readable name of a status, and the last error message of a context
  * (a static empty string when there is none; ctx may be NULL). */

@@ -1013,6 +1013,13 @@ struct nrmg_batch {
   int grid;
   int depth;
   long long launches;
+  // the batched cycle captured as a CUDA graph (after one eager cycle; legacy default stream:
+  // never captured)
+  int cycles_run;
+  int graph_state;  // 0 not tried, 1 replaying, 2 capture unavailable
+  cudaGraphExec_t gexec;
+  int graph_grid;
+  long long graph_launches;
   char err[256];
 };
 
@@ -1195,6 +1202,11 @@ nrmg_status nrmg_batch_create(nrmg_ctx *const *ctxs, int n, void *dev_workspace,
   B->stream = ctxs[0]->stream;
   B->ctl = (int *)dev_workspace;
   B->launches = 0;
+  B->cycles_run = 0;
+  B->graph_state = 0;
+  B->gexec = nullptr;
+  B->graph_grid = 0;
+  B->graph_launches = 0;
   B->err[0] = 0;
   int D = 0;
   for (int b = 0; b < n; ++b) D = std::max(D, ctxs[b]->levels - 1);
@@ -1216,6 +1228,7 @@ nrmg_status nrmg_batch_create(nrmg_ctx *const *ctxs, int n, void *dev_workspace,
 nrmg_status nrmg_batch_destroy(nrmg_batch *B) {
   if (!B) return NRMG_ERR_ARG;
   cudaStreamSynchronize(B->stream);
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
   delete B;
   return NRMG_OK;
 }
@@ -1234,7 +1247,42 @@ nrmg_status nrmg_batch_fas_cycle(nrmg_batch *B, double *rel_res_out) {
       ctx->have_res0 = 1;
     }
   }
-  if ((s = batch_cycle_async(B)) != NRMG_OK) return s;
+  if (B->graph_state == 1 && B->graph_grid != B->grid) {  // the grid changed: capture again
+    cudaGraphExecDestroy(B->gexec);
+    B->gexec = nullptr;
+    B->graph_state = 0;
+  }
+  if (B->graph_state == 1) {
+    if (cudaGraphLaunch(B->gexec, B->stream) != cudaSuccess) return NRMG_ERR_CUDA;
+    B->launches += B->graph_launches;
+  } else if (B->graph_state == 0 && B->cycles_run >= 1 && B->stream != nullptr) {
+    // capture this cycle; fall back to eager launches if capture is not possible
+    long long before = nrmg_batch_launch_count(B);
+    bool captured = false;
+    if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      s = batch_cycle_async(B);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(B->stream, &g);
+      if (s == NRMG_OK && e == cudaSuccess && g &&
+          cudaGraphInstantiate(&B->gexec, g, 0) == cudaSuccess) {
+        captured = true;
+        B->graph_launches = nrmg_batch_launch_count(B) - before;
+        B->graph_grid = B->grid;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    if (captured) {
+      B->graph_state = 1;
+      if (cudaGraphLaunch(B->gexec, B->stream) != cudaSuccess) return NRMG_ERR_CUDA;
+    } else {
+      B->graph_state = 2;
+      if ((s = batch_cycle_async(B)) != NRMG_OK) return s;
+    }
+  } else {
+    if ((s = batch_cycle_async(B)) != NRMG_OK) return s;
+  }
+  B->cycles_run += 1;
   if ((s = batch_norms(B, nr)) != NRMG_OK) return s;
   if (rel_res_out)
     for (int b = 0; b < n; ++b) rel_res_out[b] = B->ctx[b]->res0 > 0.0 ? nr[b] / B->ctx[b]->res0 : 0.0;
@@ -1277,6 +1325,8 @@ nrmg_status nrmg_batch_solve(nrmg_batch *B, double tol, int max_cycles, int *cyc
   if (s == NRMG_OK && !done()) s = NRMG_ERR_NOT_CONVERGED;
   return s;
 }
+
+int nrmg_batch_graph(const nrmg_batch *B) { return B && B->graph_state == 1 ? 1 : 0; }
 
 nrmg_status nrmg_batch_set_grid(nrmg_batch *B, int ctas_per_sm) {
   if (!B || ctas_per_sm < 1 || ctas_per_sm > std::max(1, B->ctx[0]->occ[0])) return NRMG_ERR_ARG;

@@ -105,6 +105,8 @@ def lib():
         L.nrmg_batch_fas_cycle.argtypes = [c_void_p, POINTER(c_double)]
         L.nrmg_batch_solve.restype = c_int
         L.nrmg_batch_solve.argtypes = [c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]
+        L.nrmg_batch_graph.restype = c_int
+        L.nrmg_batch_graph.argtypes = [c_void_p]
         L.nrmg_batch_set_grid.restype = c_int
         L.nrmg_batch_set_grid.argtypes = [c_void_p, c_int]
         L.nrmg_batch_launch_count.restype = c_longlong
@@ -332,6 +334,11 @@ class Batch:
     @property
     def launches(self) -> int:
         return int(self.L.nrmg_batch_launch_count(self.h))
+
+    @property
+    def graph(self) -> bool:
+        """True when the batched cycle replays a captured CUDA graph."""
+        return bool(self.L.nrmg_batch_graph(self.h))
 
     def set_grid(self, ctas_per_sm: int):
         st = self.L.nrmg_batch_set_grid(self.h, ctas_per_sm)

@@ -312,6 +312,24 @@ def test_batch_cycles_equal_individual_cycles():
         assert_close(N(Fb), N(Fg), 1e-13, "coeffs")
 
 
+def test_batch_graph_replay_equals_eager_cycles():
+    """Cycles replayed from the captured CUDA graph give the same states as eager cycles."""
+    probs = _batch_problems()[:3]
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        eager = [nrmg.from_problem(p, device=DEV, stream=st) for p in probs]
+        graph = [nrmg.from_problem(p, device=DEV, stream=st) for p in probs]
+        Be, Bg = nrmg.Batch(eager), nrmg.Batch(graph)
+        for c in range(4):
+            rg = Bg.fas_cycle()
+            # keep the eager batch eager: re-create it never captures before its 2nd cycle
+            re_ = [S.fas_cycle() for S in eager]
+            assert np.allclose(rg, re_, rtol=1e-12, atol=0)
+        assert Bg.graph
+    for a, b in zip(graph, eager):
+        assert_close(N(a.get_state()[1]), N(b.get_state()[1]), 1e-13, "coeffs")
+
+
 def test_batch_solve_matches_oracle():
     probs = _batch_problems()[:2]
     batched = [gpu(p) for p in probs]
