@@ -398,6 +398,7 @@ void layout(const nrmg_grid *g, int M, const nrmg_opts *opts, Carver &cv, nrmg_c
     L.bP = cv.take<double>(nc * 4);
     L.bF = cv.take<double>(nc * NP);
     L.D = cv.take<double>(nc * NP);
+    L.tp = cv.take<double>(nc);
     L.ver = cv.take<int>(nc);
     L.order = cv.take<int>(4 * nc);
     L.has_r = 0;
@@ -642,6 +643,7 @@ nrmg_status set_maxwellian(nrmg_ctx *ctx) {
                          cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpy2DAsync(L.P + 3, sizeof(double) * 4, ones.data(), sizeof(double), sizeof(double), L.ncell,
                          cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_tpow(ctx->K, L, ctx->stream));
     L.has_r = 0;
   }
   CK(cudaStreamSynchronize(ctx->stream));
@@ -721,6 +723,7 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
     K.beta = coll->beta;
     K.cfl = opts->cfl;
     K.dtnu = opts->dtnu;
+    K.nu0 = coll->beta * sqrt(M_PI / 2.0) / Kn;
     K.C = hermite_largest_root(M + 1);
     K.lx = grid->lx;
     K.ly = grid->ly;
@@ -803,6 +806,8 @@ nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *P, const doub
   nrmg_status s = sync_status(ctx);
   if (s == NRMG_ERR_ARG) return set_err(ctx, s, "set_state: state is not planar (u3 or an odd-alpha3 coefficient is nonzero)");
   if (s != NRMG_OK) return set_err(ctx, s, "set_state: non-physical or non-finite state");
+  CK(launch_tpow(ctx->K, L, ctx->stream));
+  ctx->launches += 1;
   if (level == ctx->levels - 1) {
     // reference mass of the correction
     int g = (int)std::min<long long>(std::max(1, (L.ncell + kThreads - 1) / kThreads), 1024);
@@ -1404,6 +1409,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   const size_t o_scal = at(64 * sizeof(double));
   const size_t o_P = at(ncell * 4 * sizeof(double));
   const size_t o_F = at(ncell * NP * sizeof(double));
+  const size_t o_tp = at(ncell * sizeof(double));
   if (used > NRMG_NOALLOC_SCRATCH_BYTES) return NRMG_ERR_OOM;
 
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -1430,6 +1436,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   K.beta = coll->beta;
   K.cfl = opts->cfl;
   K.dtnu = opts->dtnu;
+  K.nu0 = coll->beta * sqrt(M_PI / 2.0) / Kn;
   K.C = hermite_largest_root(M + 1);
   K.lx = grid->lx;
   K.ly = grid->ly;
@@ -1466,6 +1473,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   L.idy = 1.0 / L.dy;
   L.P = (double *)(b + o_P);
   L.F = (double *)(b + o_F);
+  L.tp = (double *)(b + o_tp);
   L.has_r = 0;
 
 #define NA(expr)                                  \
@@ -1483,6 +1491,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   NA(cudaMemcpyAsync(L.P, dev_params, sizeof(double) * 4 * ncell, cudaMemcpyDeviceToDevice, st));
   NA(launch_pack(dev_coeffs, N, L.F, NP, L.ncell, N, st));
   NA(launch_check_state(K, L.P, L.F, NP, L.ncell, 0, st));
+  NA(launch_tpow(K, L, st));
   int occ = occupancy_cell(M, NP, 1);
   long long g = (long long)nsm * (occ < 1 ? 1 : occ);
   if (g > ncell) g = ncell;

@@ -64,7 +64,7 @@ enum { I_ITEM = 0, I_NACT = 1, I_ACT = 2 /* ..2+kNV */, I_EX = 16 /* ..16+9 */, 
        I_BAD = 34, I_ABORT = 35 };
 // sc slots
 enum { S_DT = 0, S_NU = 1, S_Q = 2 /* ..5 */, S_W = 8 /* ..8+12: w1,w2,w3 per face */, S_RHOW = 20 /* ..24 */,
-       S_NEWP = 24 /* ..28 */, S_PH = 32 /* ..36 */, S_NORM = 40, S_RED = 44 /* ..44+8 warps */,
+       S_NEWP = 24 /* ..28 */, S_PH = 32 /* ..36 */, S_NORM = 40, S_TPN = 42, S_RED = 44 /* ..44+8 warps */,
        S_TPOW = 64 /* ..64+kMaxM+1: theta^-k */ };
 
 constexpr uint16_t kNone = 0xFFFF;
@@ -246,10 +246,21 @@ __device__ inline void macros(const Consts &K, const double *p, const double *g,
 // Half of the limited slope times the cell width, q_face = q0 +- hs (eq. moments-recon with the
 // slope of the central difference, or of the van Albada average (b^2+e)a + (a^2+e)b over
 // a^2 + b^2 + 2e = (a+b)(ab+e) / (a^2+b^2+2e), a = q0 - qm, b = qp - q0).
+// 1/x for x >= 2e-12 (normal, finite): the hardware reciprocal estimate refined by two
+// Newton-Raphson steps y <- y + y (1 - x y) (each step squares the relative error).
+__device__ inline double rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 __device__ inline double half_slope(int slope, double qm, double q0, double qp) {
   if (slope == 1) return 0.25 * (qp - qm);
   double a = q0 - qm, b = qp - q0;
-  return 0.5 * ((a + b) * fma(a, b, VA_EPS2)) / fma(a, a, fma(b, b, 2.0 * VA_EPS2));
+  return 0.5 * ((a + b) * fma(a, b, VA_EPS2)) * rcp_nr(fma(a, a, fma(b, b, 2.0 * VA_EPS2)));
 }
 
 // stencil slots: 0 C, 1 E, 2 W, 3 N, 4 S, 5 EE, 6 WW, 7 NN, 8 SS

@@ -25,6 +25,7 @@ struct LevelDev {
   double *rP, *rF;  // right-hand side r and its expansion bases
   double *bP, *bF;  // restricted state saved for the coarse-grid update
   double *D;        // defect r - R(f)
+  double *tp;       // theta^(1-omega) of each cell, written with the cell's state
   int *ver;         // per-cell update counters of the sweep scheduler
   int *order;       // [4][ncell]: cells of sweep Dk in anti-diagonal order
   int has_r;
@@ -44,6 +45,7 @@ struct Consts {
   int model;
   double Kn, Pr, omega, beta, cfl, C;  // C = largest root of He_{M+1}
   double dtnu;                         // > 0: time step capped at dtnu / nu
+  double nu0;                          // beta sqrt(pi/2) / Kn: nu = nu0 rho theta^(1-omega)
   double lx, ly;
   double wall_u[4][3], wall_theta[4];
   // tables (global memory, copied to shared memory by each CTA)
@@ -94,6 +96,8 @@ cudaError_t launch_reduce_norm(const double *partials, int n, double scale, doub
 cudaError_t launch_mass(const Consts &K, const LevelDev &L, double *partials, int grid, double *scal, double m0,
                         bool apply, cudaStream_t st);
 cudaError_t launch_fields(const Consts &K, const LevelDev &L, double *out, cudaStream_t st);
+// theta^(1-omega) of every cell of L (after its state was written from outside the sweeps)
+cudaError_t launch_tpow(const Consts &K, const LevelDev &L, cudaStream_t st);
 cudaError_t launch_pack(const double *src, int src_stride, double *dst, int dst_stride, int rows, int cols,
                         cudaStream_t st);
 // Admissibility of a state (rhs = 0) or of a right-hand side (rhs = 1) handed in through the C

@@ -131,7 +131,8 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   if (tid == 32) {
     const double *f = pc + 4;
     double rho = f[0], th = pc[3];
-    const double nu = K.beta * sqrt(M_PI / 2.0) * rho * pow(th, 1.0 - K.omega) / K.Kn;
+    const double tpc = kCoherent ? __ldcg(L.tp + c) : L.tp[c];
+    const double nu = K.nu0 * rho * tpc;
     s.sc[S_NU] = nu;
     double sq = sqrt(th);
     double dt = K.cfl / ((fabs(pc[0]) + K.C * sq) * L.idx + (fabs(pc[1]) + K.C * sq) * L.idy);
@@ -285,7 +286,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
 // Back to Grad form (Sec. 2.4): macroscopics of g (basis pc), project g into the new basis,
 // zero f_{e_d} and the round-off mean of f_{2e_d}.  g lives in VA slot `v`; the result is left
 // in VB slot `v` and the new params in sc[S_NEWP..].  Returns true when the state is physical.
-__device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v) {
+__device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v, bool want_tp = false) {
   const int tid = threadIdx.x, NP = K.NP;
   if (tid == 0) {
     double mac[5];
@@ -300,6 +301,8 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v) {
     s.iarr[I_BAD] = !(isfinite(mac[0]) && isfinite(mac[4]) && mac[0] > 0.0 && mac[4] > 0.0);
   }
   __syncthreads();
+  // theta^(1-omega) of the new state, on the last warp (idle in the one-vector transform)
+  if (want_tp && tid == kThreads - 1) s.sc[S_TPN] = pow(s.sc[S_NEWP + 3], 1.0 - K.omega);
   setup_coeffs(K, s);
   __syncthreads();
   transform_batch(K, s, s.VA, s.VB);
@@ -356,13 +359,14 @@ __device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c,
   __syncthreads();
   double pcell[4];
   for (int e = 0; e < 4; ++e) pcell[e] = s.cst[e];
-  bool ok = regrad(K, s, pcell, 4);
+  bool ok = regrad(K, s, pcell, 4, true);
   double *Fo = L.F + (size_t)c * NP;
   for (int q = tid; q < K.NE; q += kThreads) {
     const int o = s.eidx[q];
     Fo[o] = s.VB[4 * NP + o];
   }
   if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+  if (tid == 4) L.tp[c] = s.sc[S_TPN];
   if (!ok && tid == 0) raise_status(K, kStNonPhysical, true);
   __syncthreads();
   if (tid == 0) {
@@ -513,6 +517,7 @@ __global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev L
       double *pH = s.sc + S_PH;
       for (int d = 0; d < 3; ++d) pH[d] = mom[d] / rho;
       pH[3] = (en - rho * (pH[0] * pH[0] + pH[1] * pH[1] + pH[2] * pH[2])) / (3.0 * rho);
+      s.sc[S_TPN] = pow(pH[3], 1.0 - K.omega);
       for (int v = 0; v < 8; ++v) {
         for (int e = 0; e < 4; ++e) s.vdst[v * 4 + e] = pH[e];
         s.iarr[I_ACT + v] = v;
@@ -554,6 +559,7 @@ __global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev L
       Lc.bP[(size_t)C * 4 + tid] = v;
       Lc.rP[(size_t)C * 4 + tid] = v;
     }
+    if (tid == 4) Lc.tp[C] = s.sc[S_TPN];
     __syncthreads();
   }
 }
@@ -595,12 +601,13 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(Consts K, LevelDev Lf
     __syncthreads();
     double pcell[4];
     for (int e = 0; e < 4; ++e) pcell[e] = s.sc[S_PH + e];
-    bool ok = regrad(K, s, pcell, 0);
+    bool ok = regrad(K, s, pcell, 0, true);
     for (int q = tid; q < NE; q += kThreads) {
       const int o = s.eidx[q];
       Lf.F[(size_t)c * NP + o] = s.VB[o];
     }
     if (tid < 4) Lf.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+    if (tid == 4) Lf.tp[c] = s.sc[S_TPN];
     if (!ok && tid == 0) raise_status(K, kStNonPhysical, false);
     __syncthreads();
   }
@@ -663,6 +670,11 @@ __global__ void fields_kernel(Consts K, LevelDev L, double *out) {
       o[11 + a] = q;
     }
   }
+}
+
+__global__ void tpow_kernel(Consts K, LevelDev L) {
+  for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads)
+    L.tp[c] = pow(L.P[(size_t)c * 4 + 3], 1.0 - K.omega);
 }
 
 __global__ void pack_kernel(const double *src, int ss, double *dst, int ds, int rows, int cols) {
@@ -771,6 +783,13 @@ cudaError_t launch_fields(const Consts &K, const LevelDev &L, double *out, cudaS
   int g = (L.ncell + kThreads - 1) / kThreads;
   if (g > 4096) g = 4096;
   fields_kernel<<<g, kThreads, 0, st>>>(K, L, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tpow(const Consts &K, const LevelDev &L, cudaStream_t st) {
+  int g = (L.ncell + kThreads - 1) / kThreads;
+  if (g > 4096) g = 4096;
+  tpow_kernel<<<g, kThreads, 0, st>>>(K, L);
   return cudaGetLastError();
 }
 

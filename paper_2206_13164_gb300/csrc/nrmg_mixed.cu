@@ -82,7 +82,7 @@ __global__ void mixed_prep_kernel(Consts K, LevelDev L) {
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads) {
     const double *p = L.P + (size_t)c * 4;
     const double rho = L.F[(size_t)c * K.NP], th = p[3], sq = sqrt(th);
-    const double nu = K.beta * sqrt(M_PI / 2.0) * rho * pow(th, 1.0 - K.omega) / K.Kn;
+    const double nu = K.nu0 * rho * L.tp[c];
     double dt = K.cfl / ((fabs(p[0]) + K.C * sq) * L.idx + (fabs(p[1]) + K.C * sq) * L.idy);
     if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / nu);
     float *a = L.aux32 + (size_t)c * 8;
@@ -384,6 +384,7 @@ __device__ inline bool regrad_mixed(const Consts &K, Sm &s, const double *pc) {
     s.iarr[I_BAD] = !(isfinite(rho) && isfinite(th) && rho > 0.0 && th > 0.0);
   }
   __syncthreads();
+  if (tid == kThreads - 1) s.sc[S_TPN] = pow(s.sc[S_NEWP + 3], 1.0 - K.omega);
   setup_coeffs(K, s);
   __syncthreads();
   transform_batch(K, s, s.VA, s.VB);
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(kThreads) mixed_update_kernel(Consts K, LevelD
       L.F[(size_t)c * NP + o] = s.VB[o];
     }
     if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+    if (tid == 4) L.tp[c] = s.sc[S_TPN];
     if (!ok && tid == 0) atomicCAS(K.status, 0, kStNonPhysical);
     __syncthreads();
   }
