@@ -180,6 +180,12 @@ nrmg_status nrmg_two_grid_update(nrmg_ctx *ctx, int lf);
  * applied after each NMG step). */
 nrmg_status nrmg_mass_correct(nrmg_ctx *ctx);
 
+/* Failure-detection check (no counterpart in the paper): one FS launch on `level` whose
+ * update counters are preset to a value no update ever publishes, so the first dependency
+ * wait runs out after its time limit (about 2 s), every CTA leaves, and the call returns
+ * NRMG_ERR_TIMEOUT.  No cell is updated; the context stays usable.  Synchronizes. */
+nrmg_status nrmg_debug_stalled_sweep(nrmg_ctx *ctx, int level);
+
 /* Synchronize the stream and return (and clear) the device status. */
 nrmg_status nrmg_sync(nrmg_ctx *ctx);
 

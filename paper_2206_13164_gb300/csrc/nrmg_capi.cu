@@ -919,6 +919,19 @@ nrmg_status nrmg_mass_correct(nrmg_ctx *ctx) {
   return mass_correct(ctx);
 }
 
+nrmg_status nrmg_debug_stalled_sweep(nrmg_ctx *ctx, int level) {
+  if (!ctx || level < 0 || level >= ctx->levels) return NRMG_ERR_ARG;
+  LevelDev &L = ctx->lev[level];
+  // every update counter starts far below any version an update waits for: nothing ever
+  // satisfies the first wait, which runs out after its time limit
+  CK(cudaMemsetAsync(L.ver, 0x80, sizeof(int) * L.ncell, ctx->stream));
+  CK(cudaMemsetAsync(ctx->K.queue, 0, sizeof(int), ctx->stream));
+  int g = grid_for(ctx, 0, 4LL * L.ncell);
+  CK(launch_fs(ctx->K, L, 1, nullptr, g, ctx->stream));
+  ctx->launches += 1;
+  return sync_status(ctx);
+}
+
 nrmg_status nrmg_sync(nrmg_ctx *ctx) {
   if (!ctx) return NRMG_ERR_ARG;
   return sync_status(ctx);

@@ -82,6 +82,8 @@ def lib():
         L.nrmg_two_grid_update.argtypes = [c_void_p, c_int]
         L.nrmg_mass_correct.restype = c_int
         L.nrmg_mass_correct.argtypes = [c_void_p]
+        L.nrmg_debug_stalled_sweep.restype = c_int
+        L.nrmg_debug_stalled_sweep.argtypes = [c_void_p, c_int]
         L.nrmg_sync.restype = c_int
         L.nrmg_sync.argtypes = [c_void_p]
         L.nrmg_launch_count.restype = c_longlong
@@ -249,6 +251,12 @@ class Solver:
 
     def mass_correct(self):
         self._check(self.L.nrmg_mass_correct(self.ctx), "nrmg_mass_correct")
+
+    def debug_stalled_sweep(self, level=None) -> int:
+        """Status of an FS launch whose dependency waits can never be satisfied (expected:
+        ERR_TIMEOUT after the scheduler's time limit)."""
+        level = self.levels - 1 if level is None else level
+        return int(self.L.nrmg_debug_stalled_sweep(self.ctx, level))
 
     def sync(self):
         self._check(self.L.nrmg_sync(self.ctx), "nrmg_sync")

@@ -236,6 +236,44 @@ def test_non_planar_input_is_rejected():
     assert np.isfinite(n) and np.all(N(R)[:, 6] == 0.0)
 
 
+def test_scheduler_wait_times_out_and_context_recovers():
+    """A dependency wait that nothing satisfies ends after the time limit with
+    NRMG_ERR_TIMEOUT (no fault, no hang); the same context then sweeps correctly."""
+    import time
+
+    prob = lid_cavity(16, 4, 0.1, 0.3, order=2, slope=2)
+    rng = np.random.default_rng(107)
+    P, F = random_state(rng, 16, 16, 4)
+    G, O = gpu(prob), oracle_solver(prob)
+    set_both(G, O, 0, P, F)
+    t0 = time.perf_counter()
+    st = G.debug_stalled_sweep(0)
+    dt = time.perf_counter() - t0
+    assert st == nrmg.ERR_TIMEOUT and 1.0 < dt < 30.0
+    Pg, Fg = G.get_state(0)
+    assert np.array_equal(N(Fg), F)  # nothing was updated
+    G.smooth(0, 1)
+    O.smooth(0, 1)
+    assert_close(N(G.get_state(0)[1]), O.get_state(0)[1], 1e-12, "after recovery")
+
+
+def test_checkpoint_resume_reproduces_the_residual_history():
+    prob = lid_cavity(32, 5, 0.1, 0.3, order=2, slope=2, levels=3)
+    A = gpu(prob)
+    for _ in range(3):
+        A.fas_cycle()
+    P, F = A.get_state()
+    B = gpu(prob)
+    B.set_state(P.clone(), F.clone())
+    for _ in range(3):
+        A.fas_cycle()
+        B.fas_cycle()
+        _, na = A.residual()
+        _, nb = B.residual()
+        assert abs(na - nb) <= 1e-12 * na
+    assert_close(N(B.get_state()[1]), N(A.get_state()[1]), 1e-12, "resumed state")
+
+
 @pytest.mark.parametrize("which", ["c2", "c3"])
 def test_full_size_residual_sampled(which):
     """The full-size cavity workloads (256x256 M=10; 512x512 M=8 Shakhov), launched as the
