@@ -40,24 +40,42 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     s.iarr[I_EX + tid] = (ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && reach <= K.reach) ? 1 : 0;
   }
   __syncthreads();
-  // ---- stencil (params + coefficients)
-  for (int sl = 0; sl < 9; ++sl) {
-    if (!s.iarr[I_EX + sl]) continue;
-    int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
-    double *dst = stencil(s, sl, NP);
-    const double *srcP = L.P + (size_t)cc * 4, *srcF = L.F + (size_t)cc * NP;
-    for (int e = tid; e < 4 + N; e += kThreads) {
-      const double *ptr = e < 4 ? srcP + e : srcF + (e - 4);
-      dst[e] = kCoherent ? __ldcg(ptr) : *ptr;
+  // ---- stencil (params + the even-alpha_3 coefficients): each thread issues its loads
+  //      before its shared-memory stores so that they are in flight together
+  {
+    const int NE = K.NE, W = 4 + NE, tot = 9 * W;
+    constexpr int kU = 8;
+    for (int q0 = tid; q0 < tot; q0 += kU * kThreads) {
+      double v[kU];
+      double *d[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        int q = q0 + u * kThreads;
+        d[u] = nullptr;
+        if (q < tot) {
+          int sl = q / W, e = q - sl * W;
+          if (s.iarr[I_EX + sl]) {
+            int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
+            int col = e < 4 ? e : 4 + s.eidx[e - 4];
+            const double *ptr = e < 4 ? L.P + (size_t)cc * 4 + e : L.F + (size_t)cc * NP + (col - 4);
+            v[u] = kCoherent ? __ldcg(ptr) : *ptr;
+            d[u] = stencil(s, sl, NP) + col;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (d[u]) *d[u] = v[u];
     }
   }
   if (tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
   if (L.has_r) {
-    for (int e = tid; e < 4 + N; e += kThreads) {
+    for (int e = tid; e < 4 + K.NE; e += kThreads) {
       if (e < 4) {
         s.vsrc[8 * 4 + e] = L.rP[(size_t)c * 4 + e];
       } else {
-        s.VA[8 * NP + e - 4] = L.rF[(size_t)c * NP + e - 4];
+        const int o = s.eidx[e - 4];
+        s.VA[8 * NP + o] = L.rF[(size_t)c * NP + o];
       }
     }
   }
@@ -157,9 +175,10 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   }
   __syncthreads();
   // ---- HLL weights per interior face: F = w1 Xi a- + w2 Xi a+ + w3 (a+ - a-)
-  if (tid < 4 && !s.iarr[I_WALL + tid]) {
-    int ax = tid >> 1;
-    const double *pm = s.vsrc + (2 * tid) * 4, *pp = s.vsrc + (2 * tid + 1) * 4;
+  // (on warp 1, in parallel with warp 0's coefficient recurrences)
+  if (tid >= 32 && tid < 36 && !s.iarr[I_WALL + tid - 32]) {
+    const int f = tid - 32, ax = f >> 1;
+    const double *pm = s.vsrc + (2 * f) * 4, *pp = s.vsrc + (2 * f + 1) * 4;
     double sL = fmin(pm[ax] - K.C * sqrt(pm[3]), pp[ax] - K.C * sqrt(pp[3]));
     double sR = fmax(pm[ax] + K.C * sqrt(pm[3]), pp[ax] + K.C * sqrt(pp[3]));
     double w1, w2, w3;
@@ -171,9 +190,9 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
       double inv = 1.0 / (sR - sL);
       w1 = sR * inv; w2 = -sL * inv; w3 = sL * sR * inv;
     }
-    s.sc[S_W + 3 * tid] = w1;
-    s.sc[S_W + 3 * tid + 1] = w2;
-    s.sc[S_W + 3 * tid + 2] = w3;
+    s.sc[S_W + 3 * f] = w1;
+    s.sc[S_W + 3 * f + 1] = w2;
+    s.sc[S_W + 3 * f + 2] = w3;
   }
   setup_coeffs(K, s);
   __syncthreads();
@@ -309,7 +328,7 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v, b
   double *g = s.VB + v * NP;
   if (tid == 0) {
     for (int d = 0; d < 2; ++d) g[K.idx_e[d]] = 0.0;  // f_{e_3} is not formed (odd alpha_3)
-    double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) / 3.0;
+    double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) * (1.0 / 3.0);
     for (int d = 0; d < 3; ++d) g[K.idx_2e[d]] -= s3;
   }
   __syncthreads();
@@ -543,7 +562,7 @@ __global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev L
     __syncthreads();
     if (tid == 0) {
       for (int d = 0; d < 2; ++d) fH[K.idx_e[d]] = 0.0;
-      double s3 = (fH[K.idx_2e[0]] + fH[K.idx_2e[1]] + fH[K.idx_2e[2]]) / 3.0;
+      double s3 = (fH[K.idx_2e[0]] + fH[K.idx_2e[1]] + fH[K.idx_2e[2]]) * (1.0 / 3.0);
       for (int d = 0; d < 3; ++d) fH[K.idx_2e[d]] -= s3;
     }
     __syncthreads();

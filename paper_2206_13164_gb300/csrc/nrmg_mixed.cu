@@ -391,7 +391,7 @@ __device__ inline bool regrad_mixed(const Consts &K, Sm &s, const double *pc) {
   double *g = s.VB;
   if (tid == 0) {
     for (int d = 0; d < 2; ++d) g[K.idx_e[d]] = 0.0;
-    double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) / 3.0;
+    double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) * (1.0 / 3.0);
     for (int d = 0; d < 3; ++d) g[K.idx_2e[d]] -= s3;
   }
   __syncthreads();
