@@ -9,11 +9,13 @@ van Albada reconstruction, 6 levels (coarsest 8x8), s1 = s2 = 2, s3 = 4.
 metric: cell-moment updates per second = 4 sweeps x cells x N_M per FS step, summed over the
 FS steps of every level in the timed cycles (residual evaluations are not counted).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload lid256|lid32|lid64|heat512]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload lid256|lid32|lid64|heat512|batch64|learned512]
 
 The JSON line also reports the same cycle with the mixed-precision smoother (FP32 correction
-sweeps inside FP64 defect correction) and, at N=1, the wall time of both forms to relative
-residual 1e-8 from the global Maxwellian.
+sweeps inside FP64 defect correction) and, at N=1, the wall time to relative residual 1e-8 of
+the plain, mixed and learned-start forms.  --workload learned512 prints the learned start's
+line on the held-out 512x512, M=10 cavity; --workload batch64 the batched form's.
 
 With --impl reference the CPU oracle (plain serial C) is timed on the host on a bounded sample
 of the same workload.  Multi-GPU runs (torchrun) solve one independent replica per GPU.
@@ -131,6 +133,105 @@ def run_batch64(args):
 
 def nmom(M):
     return (M + 1) * (M + 2) * (M + 3) // 6
+
+
+LEARNED_KEYS = ("status", "cycles", "final_cycles", "wasted_cycles", "rel_res", "rel_res_after_climb",
+                "coarse_cycles", "t_coarse", "t_climb", "t_final", "t_total", "climb")
+
+
+def net_flops(P, cin=19, hidden=64, cout=10):
+    """Algorithmic flops of one forward pass over P pixels (real channel counts, 3x3 taps)."""
+    return 2 * P * 9 * (cin * hidden + 2 * hidden * hidden + hidden * cout)
+
+
+def net_forward_timing(net, H, W, reps=10, warmup=3):
+    """CUDA-event time of the network's forward pass on one H x W image (inputs resident)."""
+    import torch
+
+    x = torch.randn((1, H, W, net.cin), dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        net.forward(x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        net.forward(x)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return ms, net_flops(H * W) / (ms * 1e-3) / 1e12
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS)"
+    except Exception:
+        return 1900.0, "fallback 1.9 PFLOP/s bf16"
+
+
+def learned_time_to_tol(w, tol=1e-8):
+    """Time to tol of the learned start on the workload (with and without the network, and with
+    the mixed-precision smoother), or the reason it cannot run."""
+    from paper_2206_13164_gb300 import learned
+
+    if w["heat"] or not w["lid"]:
+        return {"unavailable": "the learned start covers the lid-driven cavity family only"}
+    if not os.path.exists(learned.WEIGHTS):
+        return {"unavailable": "trained weights missing: " + learned.WEIGHTS}
+    net = learned.Net.load(max_pixels=w["nx"] ** 2)
+    out = {"start_grid": w["nx"] // 8, "weights": os.path.relpath(learned.WEIGHTS, ROOT), "solver_dtnu": 1.0}
+    for key, nn, prec in (("no_net", None, 0), ("net", net, 0), ("net_mixed", net, 1)):
+        ls = learned.LearnedSolve(w["nx"], w["M"], w["Kn"], w["lid"], start=w["nx"] // 8, net=nn, precision=prec)
+        r = ls.run(tol=tol)
+        out[key] = {k: r[k] for k in LEARNED_KEYS}
+        del ls
+    return out
+
+
+def run_learned512(args):
+    """The learned initial guess on the held-out 512x512, M = 10 cavity: seconds to relative
+    residual 1e-8 (of the plain start's residual) against the plain FP64 solve."""
+    import torch
+
+    from paper_2206_13164_gb300 import learned
+
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    N, M, Kn, U = 512, 10, 0.03, 0.35
+    net = learned.Net.load(max_pixels=N * N)
+    fwd_ms, fwd_tf = net_forward_timing(net, N, N, reps=max(args.steps, 3), warmup=max(args.warmup, 3))
+    props = torch.cuda.get_device_properties(local_rank)
+    try:
+        gpu_id = "GPU-" + str(props.uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    with ClockSampler(gpu_id) as clk:
+        ev = learned.evaluate(N, M, Kn, U, net, start=64)
+    peak, src = bf16_peak()
+    t_net, t_plain = ev["net"]["t_total"], ev["plain"]["t_total"]
+    out = {"metric": "seconds to relative residual 1e-8 (learned start)", "value": t_net, "unit": "s",
+           "n_gpus": 1, "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * t_net, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 solver; bf16 network with f32 accumulation",
+           "data": "synthetic",
+           "config": {"workload": f"held-out lid-driven cavity {N}x{N}, M={M}, BGK, Kn={Kn}, lid {U}, 2nd-order "
+                                  "van Albada, 7 levels, local step capped at 1/nu; network trained on solver "
+                                  "solutions at 64x64 and 128x128, M=8",
+                      "weights": os.path.relpath(learned.WEIGHTS, ROOT), "meta": getattr(net, "meta", None)},
+           "plain": {k: ev["plain"][k] for k in ("status", "cycles", "rel_res", "t_total")},
+           "no_net": {k: ev["no_net"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
+           "net": {k: ev["net"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
+           "speedup_vs_plain": t_plain / t_net,
+           "roofline": {"bound": "tensor", "kernel": "network forward (4 conv3x3 launches, mma.sync BF16)",
+                        "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,
+                        "traffic": None, "peak_source": src, "forward_ms": fwd_ms,
+                        "flops_per_forward": net_flops(N * N)},
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
 
 
 def walls_of(w):
@@ -292,11 +393,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lid256", choices=sorted(WORKLOADS) + ["batch64"])
+    ap.add_argument("--workload", default="lid256", choices=sorted(WORKLOADS) + ["batch64", "learned512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the two solves to 1e-8")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision cycle timing")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-start solves to 1e-8")
     args = ap.parse_args()
+    if args.workload == "learned512":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the learned start has no CPU counterpart"}))
+            return
+        run_learned512(args)
+        return
     if args.workload == "batch64":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU sample"}))
@@ -447,6 +555,10 @@ def main():
                         "status": int(st)}
             del S3
         ttt["mixed_over_plain_time"] = ttt["mixed"]["seconds"] / ttt["plain_fp64"]["seconds"]
+        if not args.no_learned:
+            ttt["learned"] = learned_time_to_tol(w)
+            if "net" in ttt["learned"]:
+                ttt["learned_over_plain_time"] = ttt["learned"]["net"]["t_total"] / ttt["plain_fp64"]["seconds"]
 
     # roofline of the dominant kernel (the persistent FS sweep kernel, all levels)
     fl = u0 * flops_per_update(w["M"], w["order"], False) + u1 * flops_per_update(w["M"], w["order"], True)

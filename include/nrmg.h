@@ -180,6 +180,16 @@ nrmg_status nrmg_two_grid_update(nrmg_ctx *ctx, int lf);
  * applied after each NMG step). */
 nrmg_status nrmg_mass_correct(nrmg_ctx *ctx);
 
+/* Fix the reference of the following cycles: the total mass the correction restores
+ * (mass > 0; 0 keeps the current one) and the norm the relative residual divides by
+ * (res0 > 0; 0 keeps the current one).  While a residual reference is fixed, nrmg_solve and
+ * nrmg_batch_solve measure against it instead of the residual of the state they start from,
+ * so a solve from a predicted start stops at the same discrete residual as one from the
+ * global Maxwellian.  nrmg_set_state on the finest level clears both.  NRMG_ERR_ARG for a
+ * negative or non-finite value.  The paper has no counterpart (its solves start from the
+ * global Maxwellian). */
+nrmg_status nrmg_set_reference(nrmg_ctx *ctx, double mass, double res0);
+
 /* Failure-detection check (no counterpart in the paper): one FS launch on `level` whose
  * update counters are preset to a value no update ever publishes, so the first dependency
  * wait runs out after its time limit (about 2 s), every CTA leaves, and the call returns

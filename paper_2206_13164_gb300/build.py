@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnrmg.so")
-SOURCES = ["nrmg_kernels.cu", "nrmg_mixed.cu", "nrmg_capi.cu", "nrmg_peak.cu"]
+SOURCES = ["nrmg_kernels.cu", "nrmg_mixed.cu", "nrmg_capi.cu", "nrmg_peak.cu", "nrmg_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", INCLUDE]

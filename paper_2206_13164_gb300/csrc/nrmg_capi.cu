@@ -3,6 +3,7 @@
 // on the caller's stream.
 #include "nrmg.h"
 #include "nrmg_internal.h"
+#include "nrmg_net.h"
 
 #include <math.h>
 #include <stdio.h>
@@ -338,6 +339,7 @@ struct nrmg_ctx {
   int *hpin_i;
   double m0, res0;
   int have_res0;
+  int ref_fixed;              // res0 set by nrmg_set_reference: solves keep it
   long long launches;
   // event timing of FS launches
   int profiling;
@@ -649,6 +651,7 @@ nrmg_status set_maxwellian(nrmg_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->m0 = ctx->grid.lx * ctx->grid.ly;
   ctx->have_res0 = 0;
+  ctx->ref_fixed = 0;
   return NRMG_OK;
 }
 
@@ -796,13 +799,13 @@ nrmg_status nrmg_destroy(nrmg_ctx *ctx) {
   return NRMG_OK;
 }
 
-nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *P, const double *F) {
-  if (!ctx || level < 0 || level >= ctx->levels || !P || !F) return NRMG_ERR_ARG;
+namespace {
+// Tail of every state upload: admissibility check, theta^(1-omega) cache and, on the finest
+// level, the reference mass and residual.
+nrmg_status finish_state(nrmg_ctx *ctx, int level) {
   LevelDev &L = ctx->lev[level];
-  CK(cudaMemcpyAsync(L.P, P, sizeof(double) * 4 * L.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
-  CK(launch_pack(F, ctx->N, L.F, ctx->NP, L.ncell, ctx->N, ctx->stream));
   CK(launch_check_state(ctx->K, L.P, L.F, ctx->NP, L.ncell, 0, ctx->stream));
-  ctx->launches += 2;
+  ctx->launches += 1;
   nrmg_status s = sync_status(ctx);
   if (s == NRMG_ERR_ARG) return set_err(ctx, s, "set_state: state is not planar (u3 or an odd-alpha3 coefficient is nonzero)");
   if (s != NRMG_OK) return set_err(ctx, s, "set_state: non-physical or non-finite state");
@@ -817,6 +820,37 @@ nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *P, const doub
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->m0 = ctx->hpin[0];
     ctx->have_res0 = 0;
+    ctx->ref_fixed = 0;
+  }
+  return NRMG_OK;
+}
+}  // namespace
+
+nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *P, const double *F) {
+  if (!ctx || level < 0 || level >= ctx->levels || !P || !F) return NRMG_ERR_ARG;
+  LevelDev &L = ctx->lev[level];
+  CK(cudaMemcpyAsync(L.P, P, sizeof(double) * 4 * L.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(launch_pack(F, ctx->N, L.F, ctx->NP, L.ncell, ctx->N, ctx->stream));
+  ctx->launches += 1;
+  return finish_state(ctx, level);
+}
+
+nrmg_status nrmg_set_state_from_fields(nrmg_ctx *ctx, const double *fields) {
+  if (!ctx || !fields) return NRMG_ERR_ARG;
+  const int top = ctx->levels - 1;
+  LevelDev &L = ctx->lev[top];
+  CK(launch_grad13(fields, L.ncell, ctx->M, ctx->NP, L.P, L.F, ctx->stream));
+  ctx->launches += 1;
+  return finish_state(ctx, top);
+}
+
+nrmg_status nrmg_set_reference(nrmg_ctx *ctx, double mass, double res0) {
+  if (!ctx || !(mass >= 0.0) || !(res0 >= 0.0) || !isfinite(mass) || !isfinite(res0)) return NRMG_ERR_ARG;
+  if (mass > 0.0) ctx->m0 = mass;
+  if (res0 > 0.0) {
+    ctx->res0 = res0;
+    ctx->have_res0 = 1;
+    ctx->ref_fixed = 1;
   }
   return NRMG_OK;
 }
@@ -882,10 +916,16 @@ nrmg_status nrmg_solve(nrmg_ctx *ctx, double tol, int max_cycles, int *cycles_ou
   if (!ctx || !(tol >= 0.0) || max_cycles < 0) return NRMG_ERR_ARG;
   const int K = ctx->levels - 1;
   ctx->lev[K].has_r = 0;
-  nrmg_status s = norm_of(ctx, K, nullptr, &ctx->res0);
-  if (s != NRMG_OK) return s;
-  ctx->have_res0 = 1;
-  double rr = ctx->res0 > 0.0 ? 1.0 : 0.0;
+  double rr = 0.0;
+  nrmg_status s;
+  if (ctx->ref_fixed) {
+    if ((s = norm_of(ctx, K, nullptr, &rr)) != NRMG_OK) return s;
+    rr = ctx->res0 > 0.0 ? rr / ctx->res0 : 0.0;
+  } else {
+    if ((s = norm_of(ctx, K, nullptr, &ctx->res0)) != NRMG_OK) return s;
+    ctx->have_res0 = 1;
+    rr = ctx->res0 > 0.0 ? 1.0 : 0.0;
+  }
   int it = 0;
   while (rr > tol && it < max_cycles) {
     if ((s = nrmg_fas_cycle(ctx, &rr)) != NRMG_OK) break;
@@ -1316,6 +1356,12 @@ nrmg_status nrmg_batch_solve(nrmg_batch *B, double tol, int max_cycles, int *cyc
   for (int b = 0; b < n; ++b) {
     nrmg_ctx *ctx = B->ctx[b];
     ctx->lev[ctx->levels - 1].has_r = 0;
+    if (ctx->ref_fixed) {
+      double r = 0.0;
+      if ((s = norm_of(ctx, ctx->levels - 1, nullptr, &r)) != NRMG_OK) return s;
+      rel[b] = ctx->res0 > 0.0 ? r / ctx->res0 : 0.0;
+      continue;
+    }
     if ((s = norm_of(ctx, ctx->levels - 1, nullptr, &ctx->res0)) != NRMG_OK) return s;
     ctx->have_res0 = 1;
     rel[b] = ctx->res0 > 0.0 ? 1.0 : 0.0;

@@ -112,4 +112,7 @@ cudaError_t launch_fs_corr(const Consts &K, const LevelDev &L, int steps, const 
 cudaError_t launch_mixed_update(const Consts &K, const LevelDev &L, int grid, cudaStream_t st);
 int occupancy_corr(int M, int NP);
 
+// 13-moment Grad state of given fields (nrmg_net.cu): P [ncell][4], F [ncell][NP] in graded order.
+cudaError_t launch_grad13(const double *fields, int ncell, int M, int NP, double *P, double *F, cudaStream_t st);
+
 }  // namespace nrmg

@@ -82,6 +82,10 @@ def lib():
         L.nrmg_two_grid_update.argtypes = [c_void_p, c_int]
         L.nrmg_mass_correct.restype = c_int
         L.nrmg_mass_correct.argtypes = [c_void_p]
+        L.nrmg_set_reference.restype = c_int
+        L.nrmg_set_reference.argtypes = [c_void_p, c_double, c_double]
+        L.nrmg_set_state_from_fields.restype = c_int
+        L.nrmg_set_state_from_fields.argtypes = [c_void_p, c_void_p]
         L.nrmg_debug_stalled_sweep.restype = c_int
         L.nrmg_debug_stalled_sweep.argtypes = [c_void_p, c_int]
         L.nrmg_sync.restype = c_int
@@ -251,6 +255,16 @@ class Solver:
 
     def mass_correct(self):
         self._check(self.L.nrmg_mass_correct(self.ctx), "nrmg_mass_correct")
+
+    def set_reference(self, mass=0.0, res0=0.0):
+        """Fix the reference mass of the correction and the residual norm that relative
+        residuals divide by (0 keeps the current value)."""
+        self._check(self.L.nrmg_set_reference(self.ctx, mass, res0), "nrmg_set_reference")
+
+    def set_state_from_fields(self, fields):
+        """Finest level := the 13-moment Grad state of fields ([cells, 14] float64 CUDA)."""
+        f = fields.reshape(self.ny * self.nx, 14)
+        self._check(self.L.nrmg_set_state_from_fields(self.ctx, _ptr(f)), "nrmg_set_state_from_fields")
 
     def debug_stalled_sweep(self, level=None) -> int:
         """Status of an FS launch whose dependency waits can never be satisfied (expected:

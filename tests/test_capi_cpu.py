@@ -114,3 +114,35 @@ def test_no_cpu_fallback_without_cuda(monkeypatch):
     monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
     with pytest.raises(RuntimeError):
         nrmg.Solver(8, 8, 3, 0.1, [((0, 0, 0), 1.0, 1.0)] * 4)
+
+
+def test_net_and_learned_entry_points_check_arguments():
+    """Argument checks of the learned guess's C ABI, without touching a GPU."""
+    import ctypes
+    from ctypes import c_double, c_int, c_longlong, c_size_t, c_void_p
+
+    L = nrmg.lib()
+    L.nrmg_net_workspace_bytes.restype = c_size_t
+    L.nrmg_net_workspace_bytes.argtypes = [c_int, c_int, c_int, c_longlong]
+    assert L.nrmg_net_workspace_bytes(19, 64, 10, 4096) > 0
+    assert L.nrmg_net_workspace_bytes(19, 32, 10, 4096) < L.nrmg_net_workspace_bytes(19, 64, 10, 4096)
+    for bad in ((0, 64, 10, 4096), (65, 64, 10, 4096), (19, 48, 10, 4096), (19, 64, 17, 4096), (19, 64, 10, 0)):
+        assert L.nrmg_net_workspace_bytes(*bad) == 0, bad
+    L.nrmg_net_create.restype = c_int
+    L.nrmg_net_create.argtypes = [c_int, c_int, c_int, c_longlong, ctypes.c_ulonglong, c_void_p, c_size_t, c_void_p,
+                                  ctypes.POINTER(c_void_p)]
+    h = c_void_p()
+    assert L.nrmg_net_create(19, 64, 10, 4096, 0, None, 1 << 30, None, ctypes.byref(h)) == nrmg.ERR_ARG
+    L.nrmg_net_param_count.restype = c_longlong
+    L.nrmg_net_param_count.argtypes = [c_void_p]
+    assert L.nrmg_net_param_count(None) == 0
+    L.nrmg_learned_features.restype = c_int
+    L.nrmg_learned_features.argtypes = [c_void_p, c_int, c_int, c_double, c_double, c_double, c_double, c_void_p,
+                                        c_void_p, c_void_p]
+    assert L.nrmg_learned_features(None, 4, 4, 1.0, 1.0, 0.1, 0.2, None, None, None) == nrmg.ERR_ARG
+    L.nrmg_set_reference.restype = c_int
+    L.nrmg_set_reference.argtypes = [c_void_p, c_double, c_double]
+    assert L.nrmg_set_reference(None, 1.0, 1.0) == nrmg.ERR_ARG
+    L.nrmg_set_state_from_fields.restype = c_int
+    L.nrmg_set_state_from_fields.argtypes = [c_void_p, c_void_p]
+    assert L.nrmg_set_state_from_fields(None, None) == nrmg.ERR_ARG
