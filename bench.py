@@ -172,6 +172,21 @@ def bf16_peak():
         return 1900.0, "fallback 1.9 PFLOP/s bf16"
 
 
+def mirror_symmetry_error(fields):
+    """Largest deviation from the mirror symmetry about x = 1/2 of the bottom-heated cavity,
+    relative to each field's largest magnitude: u1, s12, s13 and q1 change sign under the
+    reflection, every other field is even."""
+    import torch
+
+    odd = torch.tensor([1 if k in (1, 6, 7, 11) else 0 for k in range(14)], device=fields.device)
+    sign = 1.0 - 2.0 * odd.to(fields.dtype)
+    mirrored = torch.flip(fields, dims=[1]) * sign
+    dev = (fields - mirrored).abs().amax(dim=(0, 1))
+    scale = fields.abs().amax(dim=(0, 1)).clamp_min(1e-300)
+    keep = scale > 1e-12
+    return float((dev[keep] / scale[keep]).max())
+
+
 def learned_time_to_tol(w, tol=1e-8):
     """Time to tol of the learned start on the workload (with and without the network, and with
     the mixed-precision smoother), or the reason it cannot run."""
@@ -553,6 +568,8 @@ def main():
             torch.cuda.synchronize(dev)
             ttt[key] = {"seconds": time.perf_counter() - t0, "cycles": cyc, "rel_residual": rr,
                         "status": int(st)}
+            if w["heat"]:
+                ttt[key]["mirror_symmetry_rel_err"] = mirror_symmetry_error(S3.fields())
             del S3
         ttt["mixed_over_plain_time"] = ttt["mixed"]["seconds"] / ttt["plain_fp64"]["seconds"]
         if not args.no_learned:

@@ -9,7 +9,8 @@ cycles of Algorithm 2 on the target grid.  The network never decides the answer:
 grid both starts, network and plain interpolation, run the same FAS cycles and the one with
 the smaller residual norm (eq. relative-residual) after them continues, and the final solve
 stops at the same 1e-8 of the plain start's residual as the plain solver
-(``Solver.set_reference``).
+(``Solver.set_reference``).  By default the network is applied only on grids no finer than
+the finest grid it was trained on; finer grids take the plain interpolation.
 
 Everything numerical runs in ``libnrmg.so`` (network forward/backward/AdamW on the tensor
 cores, the feature, target and Grad-state kernels, the solver); this file marshals arguments
@@ -234,10 +235,19 @@ class LearnedSolve:
             raise ValueError("N must be start * 2^k with k >= 1")
         self.main = [lid_solver(n, M, Kn, U, **kw) for n in self.grids]
         self.twin = [lid_solver(n, M, Kn, U, **kw) for n in self.grids] if net is not None else None
-        self.res0 = plain_res0(self.main[-1])
+        self.res0_grid = [plain_res0(s) for s in self.main]
+        self.res0 = self.res0_grid[-1]
 
-    def run(self, tol=1e-8, coarse_tol=1e-6, polish=2, judge=2, max_cycles=400):
+    def run(self, tol=1e-8, coarse_tol=1e-6, polish=2, judge=2, max_cycles=400, net_grids="trained",
+            polish_tol=None):
+        """net_grids: the grids on which the network's candidate is built: "trained" (default) =
+        the grids no finer than the finest grid of the network's training data, None = all,
+        or a list; polish_tol: below the target, after the judged cycles, keep cycling the
+        winner until its residual is polish_tol of that grid's plain start."""
         Kn, U = self.Kn, self.U
+        if net_grids == "trained":
+            sizes = (getattr(self.net, "meta", None) or {}).get("sizes")
+            net_grids = [n for n in self.grids if n <= max(sizes)] if sizes else None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, cyc_c, _ = self.coarse.solve(coarse_tol, max_cycles)
@@ -251,7 +261,7 @@ class LearnedSolve:
             pro, x = features(fields, Kn, U)
             cands = [self.main[k]]
             self.main[k].set_state_from_fields(pro)
-            if self.net is not None:
+            if self.net is not None and (net_grids is None or n in net_grids):
                 y = self.net.forward(x[None])[0]
                 try:
                     self.twin[k].set_state_from_fields(combine(pro, y, U))
@@ -270,11 +280,17 @@ class LearnedSolve:
             if len(res) > 1:
                 rec["res_net"] = res[1]
                 wasted += cyc
+            else:
+                rec["net"] = "not applied"
             log.append(rec)
             if last:
                 target = cands[w]
                 judged = cyc
             else:
+                if polish_tol is not None:
+                    cands[w].set_reference(res0=self.res0_grid[k])
+                    _, extra, _ = cands[w].solve(polish_tol, max_cycles)
+                    rec["extra_cycles"] = extra
                 fields = cands[w].fields()
         target.set_reference(mass=target.grid.lx * target.grid.ly, res0=self.res0)
         rel_start = target.residual(want_R=False)[1] / self.res0
@@ -423,7 +439,20 @@ def main(argv=None):
     ev.add_argument("--polish", type=int, default=2)
     ev.add_argument("--judge", type=int, default=2)
     ev.add_argument("--weights", default=WEIGHTS)
+    pr = sub.add_parser("profile", help="a few forward passes and training steps on one image (profiling case)")
+    pr.add_argument("--N", type=int, default=512)
+    pr.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
+    if a.cmd == "profile":
+        net = Net(max_pixels=a.N * a.N, seed=0)
+        x = torch.randn((1, a.N, a.N, CIN), dtype=torch.float32, device="cuda")
+        t = torch.randn((1, a.N, a.N, COUT), dtype=torch.float32, device="cuda")
+        for _ in range(a.reps):
+            net.forward(x)
+            net.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        print(f"profile case: {a.reps} forward passes and training steps on {a.N}x{a.N}", flush=True)
+        return
     if a.cmd == "eval":
         print(json.dumps(evaluate(a.N, a.M, a.Kn, a.U, Net.load(a.weights, max_pixels=a.N * a.N), start=a.start,
                                   polish=a.polish, judge=a.judge)), flush=True)
