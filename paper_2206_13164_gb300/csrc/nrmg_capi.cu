@@ -408,8 +408,9 @@ void layout(const nrmg_grid *g, int M, const nrmg_opts *opts, Carver &cv, nrmg_c
       L.e32 = cv.take<float>(nc * NP);
       L.d32 = cv.take<float>(nc * NP);
       L.aux32 = cv.take<float>(nc * 8);
+      L.s32 = cv.take<float>(nc * NP);
     } else {
-      L.e32 = L.d32 = L.aux32 = nullptr;
+      L.e32 = L.d32 = L.aux32 = L.s32 = nullptr;
     }
     int ns = 0;
     for (int steps : sched_steps(l, opts)) {

@@ -32,6 +32,7 @@ struct LevelDev {
   // FP32 correction sweeps (precision 1): correction e, FP64 defect rounded to FP32, and the
   // frozen per-cell coefficients (u1, u2, u3, theta, dt, nu, 0, 0)
   float *e32, *d32, *aux32;
+  float *s32;  // FP32 copy of the state's coefficients: the frozen limiter weights of the correction
 };
 
 // Everything a kernel needs besides the level: scheme constants and

@@ -2,14 +2,18 @@
 // correction (the FP32 form of the fast-sweeping smoother).
 //
 // A state f (FP64, Grad form) is improved by solving L e = d for a correction e, where
-// d = r - R(f) is the FP64 defect and L a frozen-coefficient linearization of the first-order
-// operator at f: bases, HLL weights, time steps and collision frequencies are those of f;
-// face states are cell states re-expanded into the cell's basis; the wall flux, being linear
-// in the face state, is kept as is; the collision is nu (P e - e) with P the projection onto
-// the conserved moments (the linear response of the local Maxwellian), plus the linearized
-// Shakhov heat-flux term.  The correction is swept in FP32 with exactly the cell order of the
-// FP64 smoother (Algorithm 1 applied to L e = d), then added to f in FP64 and projected back
-// to Grad form.  Because the unknown is the correction, its FP32 rounding error is relative
+// d = r - R(f) is the FP64 defect and L a frozen-coefficient linearization of the operator at
+// f: bases, HLL weights, time steps and collision frequencies are those of f; face states are
+// reconstructed from the corrections as the FP64 operator reconstructs them from the state
+// (eq. moments-recon), with the limiter's weights frozen at f (the van Albada slope
+// ((b^2+e)a + (a^2+e)b) / (a^2+b^2+2e) becomes w_a da + w_b db with w_a, w_b taken from the
+// state's differences a, b), in the face bases the state reconstructs, then re-expanded into
+// the cell basis; the wall flux, being linear in the face state, is kept as is; the collision
+// is nu (P e - e) with P the projection onto the conserved moments (the linear response of the
+// local Maxwellian), plus the linearized Shakhov heat-flux term.  The correction is swept in
+// FP32 with exactly the cell order of the FP64 smoother (Algorithm 1 applied to L e = d), then
+// added to f in FP64 and projected back to Grad form.  (A first-order L for a second-order
+// limited operator lets some modes stop contracting: the iteration then stalls near 1e-6.)  Because the unknown is the correction, its FP32 rounding error is relative
 // to e, which shrinks with the defect: the outer FP64 iteration converges to the FP64 fixed
 // point R(f) = r.
 #include "nrmg_device.cuh"
@@ -18,23 +22,25 @@ namespace nrmg {
 
 // ------------------------------------------------------------------ shared-memory layout (FP32)
 struct CLayout {
-  size_t cst, VA, VB, vsrc, vdst, cf, sc, ti32, vflag, iarr, tu16, total;
+  size_t cst, VA, VB, ss, vsrc, vdst, cf, sc, ti32, vflag, iarr, tu16, total;
 };
 
 __host__ __device__ inline CLayout make_corr_layout(int M, int N, int NP) {
   const int NE = nmom_even(M);
   CLayout s;
   size_t o = 0;
-  size_t vb = (size_t)4 * (8 + NP);
+  size_t vb = (size_t)8 * (8 + NP), va = (size_t)kNV * NP;
+  if (va > vb) vb = va;
   s.cst = o;   o = al16(o + sizeof(float) * (8 + NP));
-  s.VA = o;    o = al16(o + sizeof(float) * 4 * NP);
+  s.VA = o;    o = al16(o + sizeof(float) * kNV * NP);
   s.VB = o;    o = al16(o + sizeof(float) * vb);
-  s.vsrc = o;  o = al16(o + sizeof(float) * 4 * 4);
-  s.vdst = o;  o = al16(o + sizeof(float) * 4 * 4);
-  s.cf = o;    o = al16(o + sizeof(float) * 4 * 3 * (M + 1));
+  s.ss = o;    o = al16(o + sizeof(float) * 9 * NP);
+  s.vsrc = o;  o = al16(o + sizeof(float) * kNV * 4);
+  s.vdst = o;  o = al16(o + sizeof(float) * kNV * 4);
+  s.cf = o;    o = al16(o + sizeof(float) * kNV * 3 * (M + 1));
   s.sc = o;    o = al16(o + sizeof(float) * 64);
   s.ti32 = o;  o = al16(o + sizeof(int) * (3 * NE + N));
-  s.vflag = o; o = al16(o + sizeof(int) * 4 * 3);
+  s.vflag = o; o = al16(o + sizeof(int) * kNV * 3);
   s.iarr = o;  o = al16(o + sizeof(int) * 64);
   s.tu16 = o;  o = al16(o + sizeof(uint16_t) * (13 * N + NE));
   s.total = o;
@@ -65,9 +71,20 @@ __device__ inline SmT<float> bind_corr(char *base, int M, int N, int NP) {
   return s;
 }
 
-// correction stencil slots: 0 C, 1 E, 2 W, 3 N, 4 S; the cell row is [aux(8) | e(NP)]
+// correction stencil slots: 0 C, 1 E, 2 W, 3 N, 4 S, 5 EE, 6 WW, 7 NN, 8 SS; a row is
+// [aux(8) | e(NP)]; the FP32 state of the same cells (limiter weights) sits in its own region
 __device__ inline float *cstencil(const SmT<float> &s, int sl, int NP) {
   return sl == 0 ? s.cst : s.VB + (size_t)(sl - 1) * (8 + NP);
+}
+__device__ inline float *corr_state(char *base, int M, int N, int NP) {
+  return (float *)(base + make_corr_layout(M, N, NP).ss);
+}
+
+// half of the limited slope of the frozen face bases (FP32 twin of the FP64 reconstruction)
+__device__ inline float half_slope_f(int slope, float qm, float q0, float qp) {
+  if (slope == 1) return 0.25f * (qp - qm);
+  float a = q0 - qm, b = qp - q0;
+  return 0.5f * ((a + b) * fmaf(a, b, 1e-12f)) / fmaf(a, a, fmaf(b, b, 2e-12f));
 }
 
 enum { C_DT = 0, C_NU = 1, C_Q = 2 /* ..5 */, C_W = 8 /* ..8+12 */, C_RHOW = 20 /* ..24 */ };
@@ -78,6 +95,7 @@ __global__ void mixed_prep_kernel(Consts K, LevelDev L) {
   for (size_t q = (size_t)blockIdx.x * kThreads + threadIdx.x; q < tot; q += (size_t)gridDim.x * kThreads) {
     L.d32[q] = (float)L.D[q];
     L.e32[q] = 0.0f;
+    L.s32[q] = (float)L.F[q];
   }
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads) {
     const double *p = L.P + (size_t)c * 4;
@@ -98,6 +116,7 @@ __global__ void mixed_prep_kernel(Consts K, LevelDev L) {
 __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L, int steps, const int *queue) {
   extern __shared__ __align__(16) char smem_raw[];
   SmT<float> s = bind_corr(smem_raw, K.M, K.N, K.NP);
+  float *ss = corr_state(smem_raw, K.M, K.N, K.NP);
   const int tid = threadIdx.x, N = K.N, NP = K.NP, NE = K.NE, M = K.M;
   for (int e = tid; e < 3 * NE + N; e += kThreads) s.tslot[e] = K.tab_i32[e];
   for (int e = tid; e < 13 * N + NE; e += kThreads) s.tmem[e] = K.tab_u16[e];
@@ -127,11 +146,11 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     }
     const int i = c % L.nx, j = c / L.nx;
     const int v = 4 * st + k + 1;
-    // ---- first-order cross stencil: wait for the versions of the serial order
-    if (tid < 5) {
+    // ---- cross stencil of the scheme's reach: wait for the versions of the serial order
+    if (tid < 9) {
       int di = c_nb_di[tid], dj = c_nb_dj[tid];
       int ii = i + di, jj = j + dj;
-      bool in = ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny;
+      bool in = ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && abs(di) + abs(dj) <= K.reach;
       s.iarr[I_EX + tid] = in ? 1 : 0;
       if (in) {
         int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
@@ -155,49 +174,112 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     if (tid == 0) s.iarr[I_ABORT] = ld_volatile(K.abort_flag);
     __syncthreads();
     if (s.iarr[I_ABORT]) break;
-    // ---- stencil: frozen coefficients and current corrections (even alpha_3 entries)
-    for (int sl = 0; sl < 5; ++sl) {
-      if (!s.iarr[I_EX + sl]) continue;
-      int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
-      float *dst = cstencil(s, sl, NP);
-      for (int q = tid; q < 8 + NE; q += kThreads) {
-        if (q < 8)
-          dst[q] = __ldcg(L.aux32 + (size_t)cc * 8 + q);
-        else {
-          int o = s.eidx[q - 8];
-          dst[8 + o] = __ldcg(L.e32 + (size_t)cc * NP + o);
+    // ---- stencil: frozen coefficients, current corrections and the FP32 state (even alpha_3)
+    {
+      const int W = 8 + 2 * NE, tot = 9 * W;
+      for (int q = tid; q < tot; q += kThreads) {
+        int sl = q / W, e = q - sl * W;
+        if (!s.iarr[I_EX + sl]) continue;
+        int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
+        if (e < 8) {
+          cstencil(s, sl, NP)[e] = __ldcg(L.aux32 + (size_t)cc * 8 + e);
+        } else if (e < 8 + NE) {
+          int o = s.eidx[e - 8];
+          cstencil(s, sl, NP)[8 + o] = __ldcg(L.e32 + (size_t)cc * NP + o);
+        } else {
+          int o = s.eidx[e - 8 - NE];
+          ss[sl * NP + o] = L.s32[(size_t)cc * NP + o];  // written before the launch
         }
       }
     }
     if (tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
     __syncthreads();
     const float *ac = s.cst, *ec = s.cst + 8;  // own frozen coefficients, own correction
-    // ---- vectors: neighbour corrections into the cell basis, or the cell's into the wall basis
-    for (int q = tid; q < 4 * NE; q += kThreads) {
-      int f = q / NE, o = s.eidx[q - f * NE];
-      const float *src = s.iarr[I_WALL + f] ? s.cst : cstencil(s, c_face_nb[f], NP);
-      s.VA[f * NP + o] = src[8 + o];
+    // ---- face states of the correction, slots as in the FP64 operator: 2f / 2f+1 = face f's
+    //      left / right state (E, W, N, S), or 2f = the cell in the wall basis at a wall
+    {
+      const bool slopes = K.reach == 2 && K.slope != 0;
+      const int tot = 6 * (4 + NE);
+      for (int q = tid; q < tot; q += kThreads) {
+        int it = q / (4 + NE), e = q - it * (4 + NE);
+        int X = c_it_x[it], Xm = c_it_m[it], Xp = c_it_p[it];
+        if (!s.iarr[I_EX + X]) continue;
+        bool on = slopes && s.iarr[I_EX + Xm] && s.iarr[I_EX + Xp];
+        const float *rx = cstencil(s, X, NP);
+        float q0, hs = 0.0f;
+        if (e < 4) {  // face basis: the reconstructed params of the state
+          q0 = rx[e];
+          if (on) hs = half_slope_f(K.slope, cstencil(s, Xm, NP)[e], q0, cstencil(s, Xp, NP)[e]);
+        } else {      // correction: the limited slope linearized with frozen weights
+          e = 4 + s.eidx[e - 4];
+          const int o = e - 4;
+          q0 = rx[8 + o];
+          if (on) {
+            const float em = cstencil(s, Xm, NP)[8 + o], ep = cstencil(s, Xp, NP)[8 + o];
+            if (K.slope == 1) {
+              hs = 0.25f * (ep - em);
+            } else {
+              const float a = ss[X * NP + o] - ss[Xm * NP + o], b = ss[Xp * NP + o] - ss[X * NP + o];
+              const float den = fmaf(a, a, fmaf(b, b, 2e-12f));
+              hs = 0.5f * (fmaf(b, b, 1e-12f) * (q0 - em) + fmaf(a, a, 1e-12f) * (ep - q0)) / den;
+            }
+          }
+        }
+        int v0, v1 = -1;
+        float x0, x1 = 0.0f;
+        switch (it) {
+          case 0:
+            v0 = 0; x0 = q0 + hs;
+            if (s.iarr[I_WALL + 1]) { v1 = 2; x1 = q0; } else { v1 = 3; x1 = q0 - hs; }
+            break;
+          case 1:
+            v0 = 4; x0 = q0 + hs;
+            if (s.iarr[I_WALL + 3]) { v1 = 6; x1 = q0; } else { v1 = 7; x1 = q0 - hs; }
+            break;
+          case 2: v0 = 1; x0 = q0 - hs; break;
+          case 3: v0 = 2; x0 = q0 + hs; break;
+          case 4: v0 = 5; x0 = q0 - hs; break;
+          default: v0 = 6; x0 = q0 + hs; break;
+        }
+        if (e < 4) {
+          s.vsrc[v0 * 4 + e] = x0;
+          if (v1 >= 0) s.vsrc[v1 * 4 + e] = x1;
+        } else {
+          s.VA[v0 * NP + e - 4] = x0;
+          if (v1 >= 0) s.VA[v1 * NP + e - 4] = x1;
+        }
+      }
     }
-    if (tid < 16) {
-      int f = tid >> 2, e = tid & 3;
-      if (s.iarr[I_WALL + f]) {
+    // destination bases: the cell, or the wall for a wall face's slot 2f
+    if (tid < 32) {
+      int vv = tid >> 2, e = tid & 3, f = vv >> 1;
+      if (s.iarr[I_WALL + f] && !(vv & 1)) {
         int w = c_face_wall[f];
-        s.vsrc[f * 4 + e] = ac[e];
-        s.vdst[f * 4 + e] = e < 3 ? (float)K.wall_u[w][e] : (float)K.wall_theta[w];
+        s.vdst[vv * 4 + e] = e < 3 ? (float)K.wall_u[w][e] : (float)K.wall_theta[w];
       } else {
-        s.vsrc[f * 4 + e] = cstencil(s, c_face_nb[f], NP)[e];
-        s.vdst[f * 4 + e] = ac[e];
+        s.vdst[vv * 4 + e] = ac[e];
       }
     }
     if (tid == 32) {
-      for (int f = 0; f < 4; ++f) s.iarr[I_ACT + f] = f;
-      s.iarr[I_NACT] = 4;
+      int na = 0;
+      for (int f = 0; f < 4; ++f) {
+        s.iarr[I_ACT + na++] = 2 * f;
+        if (!s.iarr[I_WALL + f]) s.iarr[I_ACT + na++] = 2 * f + 1;
+      }
+      s.iarr[I_NACT] = na;
     }
-    // frozen HLL weights of the first-order face states (cell states)
+    if (tid >= 96 && tid < 99 && K.model == 1) {
+      int ii = tid - 96;
+      const int *iq = K.tab_i32 + K.iq_off + 4 * ii;
+      float qv = 2.0f * ec[iq[0]];
+      for (int d = 0; d < 3; ++d) qv += ec[iq[1 + d]];
+      s.sc[C_Q + ii] = (ii == 2) ? 0.0f : qv;  // q_3 involves only odd alpha_3 entries
+    }
+    __syncthreads();
+    // frozen HLL weights of the reconstructed face bases
     if (tid >= 64 && tid < 68 && !s.iarr[I_WALL + tid - 64]) {
       int f = tid - 64, ax = f >> 1;
-      const float *nb = cstencil(s, c_face_nb[f], NP);
-      const float *pl = (f & 1) ? nb : ac, *pr = (f & 1) ? ac : nb;  // left / right states
+      const float *pl = s.vsrc + (2 * f) * 4, *pr = s.vsrc + (2 * f + 1) * 4;
       float sL = fminf(pl[ax] - Cf * sqrtf(pl[3]), pr[ax] - Cf * sqrtf(pr[3]));
       float sR = fmaxf(pl[ax] + Cf * sqrtf(pl[3]), pr[ax] + Cf * sqrtf(pr[3]));
       float w1, w2, w3;
@@ -213,21 +295,13 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       s.sc[C_W + 3 * f + 1] = w2;
       s.sc[C_W + 3 * f + 2] = w3;
     }
-    if (tid >= 96 && tid < 99 && K.model == 1) {
-      int ii = tid - 96;
-      const int *iq = K.tab_i32 + K.iq_off + 4 * ii;
-      float q = 2.0f * ec[iq[0]];
-      for (int d = 0; d < 3; ++d) q += ec[iq[1 + d]];
-      s.sc[C_Q + ii] = (ii == 2) ? 0.0f : q;  // q_3 involves only odd alpha_3 entries
-    }
-    __syncthreads();
     setup_coeffs(K, s);
     __syncthreads();
     transform_batch(K, s, s.VA, s.VB);
     // ---- wall fluxes (linear in the face state)
     if (tid < 4 && s.iarr[I_WALL + tid]) {
       int w = c_face_wall[tid], ax = c_wall_axis[w];
-      const float *a = s.VB + tid * NP;
+      const float *a = s.VB + (2 * tid) * NP;
       const float *wr = K.wallRf + w * (M + 1);
       float rw = 0.0f;
       for (int m = 0; m <= M; ++m) rw = fmaf(wr[m], a[K.idx_axis[ax][m]], rw);
@@ -245,23 +319,23 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         int o = pk & 2047, s0 = (pk >> 11) & 2047, p = pk >> 22;
         int b0 = s0 - p, deg = s.tdeg[o];
         int Lm = M - (deg - p);
-        const float *a = s.VB + f * NP;
-        const float *W = K.wallWf + (size_t)w * (M + 1) * (M + 1) + p * (M + 1);
+        const float *a = s.VB + (2 * f) * NP;
+        const float *Wm = K.wallWf + (size_t)w * (M + 1) * (M + 1) + p * (M + 1);
         const uint16_t *mem = s.tmem + ax * N;
         float g = 0.0f;
-        for (int m = 0; m <= Lm; ++m) g = fmaf(a[mem[b0 + m]], W[m], g);
+        for (int m = 0; m <= Lm; ++m) g = fmaf(a[mem[b0 + m]], Wm[m], g);
         if (deg == p) g = fmaf(s.sc[C_RHOW + f], K.wallInf[w * (M + 1) + p], g);
-        s.VA[f * NP + o] = g;
+        s.VA[(2 * f) * NP + o] = g;
       }
       if (tid == 0) {
-        for (int kk = 0; kk < nw; ++kk) s.iarr[I_ACT + kk] = wf[kk];
+        for (int kk = 0; kk < nw; ++kk) s.iarr[I_ACT + kk] = 2 * wf[kk];
         s.iarr[I_NACT] = nw;
       }
       if (tid < 4 && s.iarr[I_WALL + tid]) {
         int w = c_face_wall[tid];
         for (int e = 0; e < 4; ++e) {
-          s.vsrc[tid * 4 + e] = e < 3 ? (float)K.wall_u[w][e] : (float)K.wall_theta[w];
-          s.vdst[tid * 4 + e] = ac[e];
+          s.vsrc[(2 * tid) * 4 + e] = e < 3 ? (float)K.wall_u[w][e] : (float)K.wall_theta[w];
+          s.vdst[(2 * tid) * 4 + e] = ac[e];
         }
       }
       __syncthreads();
@@ -280,11 +354,10 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       for (int fc = 0; fc < 4; ++fc) {
         int ax = fc >> 1;
         float sg = (fc & 1) ? -1.0f : 1.0f;
-        float tv = s.VB[fc * NP + o];
         if (s.iarr[I_WALL + fc]) {
-          ee[ax] = fmaf(sg, tv, ee[ax]);
+          ee[ax] = fmaf(sg, s.VB[(2 * fc) * NP + o], ee[ax]);
         } else {
-          float am = (fc & 1) ? tv : ec[o], ap = (fc & 1) ? ec[o] : tv;
+          float am = s.VB[(2 * fc) * NP + o], ap = s.VB[(2 * fc + 1) * NP + o];
           float w1 = s.sc[C_W + 3 * fc], w2 = s.sc[C_W + 3 * fc + 1], w3 = s.sc[C_W + 3 * fc + 2];
           d[ax] = fmaf(sg, fmaf(w1, am, w2 * ap), d[ax]);
           ee[ax] = fmaf(sg * w3, ap - am, ee[ax]);

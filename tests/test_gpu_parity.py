@@ -323,6 +323,29 @@ def test_mixed_precision_reaches_the_fp64_solution(name, prob):
     assert n_final <= 1.0000001e-8 * O.res0()
 
 
+@pytest.mark.parametrize("prob", [
+    heated_cavity(128, 8, 0.05, theta_bottom=2.0, order=2, slope=2, levels=5),
+    lid_cavity(128, 10, 0.01, 0.5, order=2, slope=2, levels=5),
+], ids=["heated_128_M8_vanalbada", "lid_128_M10_vanalbada"])
+def test_mixed_precision_keeps_the_fp64_rate_with_a_limiter(prob):
+    """With the van Albada limiter the correction operator must carry the linearized
+    reconstruction: the mixed cycle then converges at the FP64 cycle's rate (a first-order
+    correction operator stalled here near 4e-6 with a visibly asymmetric heated solution)."""
+    P = nrmg.from_problem(prob, device=DEV)
+    stp, cp, rp = P.solve(1e-8, 200)
+    assert stp == 0
+    G = nrmg.from_problem(prob, device=DEV, precision=1)
+    stg, cg, rg = G.solve(1e-8, 200)
+    assert stg == 0 and rg <= 1e-8, (stg, cg, rg)
+    assert cg <= 1.15 * cp + 2, (cg, cp)  # frozen limiter weights: a Picard linearization
+    # two iterations stopped at residual 1e-8 differ by the discrete problem's conditioning
+    # times 1e-8: ~1e-6 of the small thermal-creep velocity here
+    fg, fp = N(G.fields()), N(P.fields())
+    for k, nm in enumerate(FIELDS):
+        scale = max(np.abs(fp[..., k]).max(), 1e-3 * np.abs(fp[..., 0]).max())
+        assert np.abs(fg[..., k] - fp[..., k]).max() <= 1e-5 * scale, nm
+
+
 # ------------------------------------------------------------------ batches (one persistent launch per stage)
 def _batch_problems():
     return [lid_cavity(32, 5, 0.1, 0.3, order=2, slope=2, levels=3),
