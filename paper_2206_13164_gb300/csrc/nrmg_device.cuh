@@ -194,8 +194,14 @@ __device__ inline T transform_one(const T *x, const T *c, const uint16_t *mem, i
 // zero) the others stay exactly zero, and directions 1, 2 and the even-k direction-3 series
 // map even alpha_3 onto even alpha_3.  Each thread forms two outputs at a time (independent
 // FMA chains: dependent FP64 latency, not throughput, limits a single cell update).
+// Barrier over the first n threads of the CTA (named barrier 1, n a multiple of 32): every
+// warp below n / 32 must reach it, and no other warp may.
+__device__ __forceinline__ void bar_first(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+
+// nbar < kThreads: the passes synchronize only the first nbar threads (the caller guarantees
+// that threads from nbar on have no output, i.e. na * NE <= nbar).
 template <typename T>
-__device__ inline void transform_batch(const Consts &K, SmT<T> &s, T *X, T *Y) {
+__device__ inline void transform_batch(const Consts &K, SmT<T> &s, T *X, T *Y, int nbar = kThreads) {
   const int N = K.N, NE = K.NE, NP = K.NP, M = K.M, na = s.iarr[I_NACT];
   const int tot = na * NE;
   for (int d = 0; d < 3; ++d) {
@@ -224,7 +230,10 @@ __device__ inline void transform_batch(const Consts &K, SmT<T> &s, T *X, T *Y) {
       out[v * NP + o] = y0;
       if (q2 < tot) out[v2 * NP + o2] = y1;
     }
-    __syncthreads();
+    if (nbar == kThreads)
+      __syncthreads();
+    else
+      bar_first(nbar);
   }
 }
 

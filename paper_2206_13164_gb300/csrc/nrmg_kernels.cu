@@ -320,18 +320,30 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v, b
     s.iarr[I_BAD] = !(isfinite(mac[0]) && isfinite(mac[4]) && mac[0] > 0.0 && mac[4] > 0.0);
   }
   __syncthreads();
-  // theta^(1-omega) of the new state, on the last warp (idle in the one-vector transform)
-  if (want_tp && tid == kThreads - 1) s.sc[S_TPN] = pow(s.sc[S_NEWP + 3], 1.0 - K.omega);
-  setup_coeffs(K, s);
-  __syncthreads();
-  transform_batch(K, s, s.VA, s.VB);
+  // theta^(1-omega) of the new state, on the last warp.  When the one-vector transform leaves
+  // that warp without outputs (N_E <= kThreads - 32), the other warps synchronize among
+  // themselves until the final barrier, so the power's latency overlaps the transform.
+  const bool split = want_tp && K.NE <= kThreads - 32;
+  const int nbar = split ? kThreads - 32 : kThreads;
   double *g = s.VB + v * NP;
-  if (tid == 0) {
-    for (int d = 0; d < 2; ++d) g[K.idx_e[d]] = 0.0;  // f_{e_3} is not formed (odd alpha_3)
-    double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) * (1.0 / 3.0);
-    for (int d = 0; d < 3; ++d) g[K.idx_2e[d]] -= s3;
+  if (want_tp && tid == kThreads - 1) s.sc[S_TPN] = pow(s.sc[S_NEWP + 3], 1.0 - K.omega);
+  if (!split || tid < kThreads - 32) {
+    setup_coeffs(K, s);
+    if (split)
+      bar_first(nbar);
+    else
+      __syncthreads();
+    transform_batch(K, s, s.VA, s.VB, nbar);
+    if (tid == 0) {
+      for (int d = 0; d < 2; ++d) g[K.idx_e[d]] = 0.0;  // f_{e_3} is not formed (odd alpha_3)
+      double s3 = (g[K.idx_2e[0]] + g[K.idx_2e[1]] + g[K.idx_2e[2]]) * (1.0 / 3.0);
+      for (int d = 0; d < 3; ++d) g[K.idx_2e[d]] -= s3;
+    }
+    if (split)
+      bar_first(nbar);
+    else
+      __syncthreads();
   }
-  __syncthreads();
   int bad = 0;
   for (int q = tid; q < K.NE; q += kThreads) bad |= !isfinite(g[s.eidx[q]]);
   bad = __syncthreads_or(bad);
