@@ -135,6 +135,11 @@ def nmom(M):
     return (M + 1) * (M + 2) * (M + 3) // 6
 
 
+# DRAM bytes (read + write) per FS launch, averaged over the 11 FS launches of one V-cycle of
+# the 256x256 M=10 workload, from one ncu capture of the current sweep kernel; no figure for
+# the other workloads
+FS_TRAFFIC_BYTES_PER_LAUNCH = {"lid256": 405.8e6}
+
 LEARNED_KEYS = ("status", "cycles", "final_cycles", "wasted_cycles", "rel_res", "rel_res_after_climb",
                 "coarse_cycles", "t_coarse", "t_climb", "t_final", "t_total", "climb")
 
@@ -269,10 +274,13 @@ def cycle_updates(w):
     return tot
 
 
-def flops_per_corr_update(M):
-    """FP32 flops of one correction-sweep cell update (first-order linearized operator, no
-    re-projection): 4 basis transforms + 60 flops per moment."""
-    return 4 * 6 * math.comb(M + 3, 4) + 60 * nmom(M)
+def flops_per_corr_update(M, order=2):
+    """FP32 flops of one correction-sweep cell update (the linearized operator, no
+    re-projection): at second order the 8 face states re-expanded into the cell basis
+    (8 transforms) + 80 flops per moment (slopes, fluxes, collision); at first order the 4
+    neighbours (4 transforms) + 60 flops per moment."""
+    T = 6 * math.comb(M + 3, 4)
+    return (8 * T + 80 * nmom(M)) if order == 2 else (4 * T + 60 * nmom(M))
 
 
 def flops_per_update(M, order, has_r):
@@ -540,7 +548,7 @@ def main():
         mlev = S2.fs_profile_levels()
         cms, cn, cu0, cu1 = S2.fs_profile()
         S2.set_profiling(False)
-        corr_fl = (cu0 + cu1) * flops_per_corr_update(w["M"])
+        corr_fl = (cu0 + cu1) * flops_per_corr_update(w["M"], w["order"])
         fp32_peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
         mixed = {"value": cycle_updates(w) * args.steps * world / (mms * 1e-3), "unit": "cell-moment updates/s",
                  "ms_per_step": mms / args.steps, "dtype": "f32 correction sweeps + f64 defect/transfers",
@@ -550,7 +558,7 @@ def main():
                               "peak": fp32_peak, "unit": "TFLOP/s",
                               "frac": (corr_fl / (cms * 1e-3) / 1e12 / fp32_peak) if cms > 0 else None,
                               "peak_source": "derived: SMs x 128 FFMA/clk x 2 flops x 2070 MHz",
-                              "flops_per_cell_update": flops_per_corr_update(w["M"]),
+                              "flops_per_cell_update": flops_per_corr_update(w["M"], w["order"]),
                               "sweep_ms_per_step": cms / args.steps,
                               "sweep_ms_per_step_by_level": [round(m / args.steps, 3) for m, _ in mlev]}}
         del S2
@@ -601,7 +609,10 @@ def main():
                        "parallelism": f"replicas x{world}", "rel_residual_after": rel},
             "roofline": {"bound": "alu", "kernel": "fs_kernel (persistent FS sweep, all levels)",
                          "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
-                         "frac": (achieved / peak_nominal) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak_nominal) if achieved else None,
+                         "traffic": FS_TRAFFIC_BYTES_PER_LAUNCH.get(args.workload),
+                         "traffic_note": "bytes per FS launch, average over one V-cycle's launches "
+                                         "(ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                          "peak_source": "derived: SMs x 2 DFMA/clk x 2 flops x 2070 MHz (FP64 pipe)",
                          "fp64_fma_measured_tflops": fp64_peak_meas / 1e12,
                          "fs_ms_per_step": fs_ms / args.steps, "fs_launches": fs_n,
