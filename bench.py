@@ -192,7 +192,7 @@ def mirror_symmetry_error(fields):
     return float((dev[keep] / scale[keep]).max())
 
 
-def learned_time_to_tol(w, tol=1e-8):
+def learned_time_to_tol(w, tol=1e-8, grid=0, grid_mixed=None):
     """Time to tol of the learned start on the workload (with and without the network, and with
     the mixed-precision smoother), or the reason it cannot run."""
     from paper_2206_13164_gb300 import learned
@@ -205,6 +205,7 @@ def learned_time_to_tol(w, tol=1e-8):
     out = {"start_grid": w["nx"] // 8, "weights": os.path.relpath(learned.WEIGHTS, ROOT), "solver_dtnu": 1.0}
     for key, nn, prec in (("no_net", None, 0), ("net", net, 0), ("net_mixed", net, 1)):
         ls = learned.LearnedSolve(w["nx"], w["M"], w["Kn"], w["lid"], start=w["nx"] // 8, net=nn, precision=prec)
+        ls.set_grid(grid if prec == 0 or grid_mixed is None else grid_mixed)
         r = ls.run(tol=tol)
         out[key] = {k: r[k] for k in LEARNED_KEYS}
         del ls
@@ -230,8 +231,14 @@ def run_learned512(args):
         gpu_id = "GPU-" + str(props.uuid)
     except Exception:
         gpu_id = str(local_rank)
+    # sweep grid picked on a throwaway context of the same cavity (untimed)
+    tuner = learned.lid_solver(N, M, Kn, U)
+    tuner.fas_cycle()
+    tune = tuner.autotune(candidates=(1, 2, 3), reps=1)
+    grid = tuner.tuned
+    del tuner
     with ClockSampler(gpu_id) as clk:
-        ev = learned.evaluate(N, M, Kn, U, net, start=64)
+        ev = learned.evaluate(N, M, Kn, U, net, start=64, grid=grid)
     peak, src = bf16_peak()
     t_net, t_plain = ev["net"]["t_total"], ev["plain"]["t_total"]
     out = {"metric": "seconds to relative residual 1e-8 (learned start)", "value": t_net, "unit": "s",
@@ -241,7 +248,8 @@ def run_learned512(args):
            "config": {"workload": f"held-out lid-driven cavity {N}x{N}, M={M}, BGK, Kn={Kn}, lid {U}, 2nd-order "
                                   "van Albada, 7 levels, local step capped at 1/nu; network trained on solver "
                                   "solutions at 64x64 and 128x128, M=8",
-                      "weights": os.path.relpath(learned.WEIGHTS, ROOT), "meta": getattr(net, "meta", None)},
+                      "weights": os.path.relpath(learned.WEIGHTS, ROOT), "meta": getattr(net, "meta", None),
+                      "autotune_ctas_per_sm": grid, "autotune_s_per_cycle": tune},
            "plain": {k: ev["plain"][k] for k in ("status", "cycles", "rel_res", "t_total")},
            "no_net": {k: ev["no_net"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
            "net": {k: ev["net"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
@@ -460,6 +468,8 @@ def main():
     fp64_peak_meas = nrmg.peak_fma(0, 2048, stream)
     for _ in range(args.warmup):
         S.fas_cycle()
+    # sweep grid: persistent CTAs per SM picked by timing one cycle each (untimed warm-up)
+    tune_plain = S.autotune(candidates=(1, 2, 3), reps=1)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = None
     try:
@@ -527,12 +537,13 @@ def main():
     bytes_state = (hP.numel() + hF.numel()) * 8
 
     # mixed precision: FP32 correction sweeps inside FP64 defect correction, same cycle
-    mixed = None
+    mixed, mixed_grid = None, 0
     if not args.no_mixed:
         S2 = nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
                          Pr=w["Pr"], order=w["order"], slope=w["slope"], precision=1, device=dev)
         for _ in range(args.warmup):
             S2.fas_cycle()
+        tune_mixed = S2.autotune(reps=1)
         S2.set_profiling(True)
         S2.fs_profile()
         barrier()
@@ -561,6 +572,9 @@ def main():
                               "flops_per_cell_update": flops_per_corr_update(w["M"], w["order"]),
                               "sweep_ms_per_step": cms / args.steps,
                               "sweep_ms_per_step_by_level": [round(m / args.steps, 3) for m, _ in mlev]}}
+        mixed_grid = S2.tuned
+        mixed["autotune_ctas_per_sm"] = S2.tuned
+        mixed["autotune_s_per_cycle"] = tune_mixed
         del S2
 
     # time to relative residual 1e-8 from the global Maxwellian, plain FP64 vs mixed
@@ -570,6 +584,7 @@ def main():
         for prec, key in ((0, "plain_fp64"), (1, "mixed")):
             S3 = nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
                              Pr=w["Pr"], order=w["order"], slope=w["slope"], precision=prec, device=dev)
+            S3.set_grid(S.tuned if prec == 0 or mixed is None else mixed_grid)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             st, cyc, rr = S3.solve(1e-8, 400)
@@ -581,7 +596,7 @@ def main():
             del S3
         ttt["mixed_over_plain_time"] = ttt["mixed"]["seconds"] / ttt["plain_fp64"]["seconds"]
         if not args.no_learned:
-            ttt["learned"] = learned_time_to_tol(w)
+            ttt["learned"] = learned_time_to_tol(w, grid=S.tuned, grid_mixed=mixed_grid if mixed else None)
             if "net" in ttt["learned"]:
                 ttt["learned_over_plain_time"] = ttt["learned"]["net"]["t_total"] / ttt["plain_fp64"]["seconds"]
 
@@ -606,7 +621,8 @@ def main():
                        "cell_moment_updates_per_step": cycle_updates(w),
                        "l2": "inputs larger than L2 (finest-level coefficient array alone is "
                              f"{w['nx'] ** 2 * ((nmom(w['M']) + 3) // 4 * 4) * 8 / 1e6:.0f} MB)",
-                       "parallelism": f"replicas x{world}", "rel_residual_after": rel},
+                       "parallelism": f"replicas x{world}", "rel_residual_after": rel,
+                       "autotune_ctas_per_sm": S.tuned, "autotune_s_per_cycle": tune_plain},
             "roofline": {"bound": "alu", "kernel": "fs_kernel (persistent FS sweep, all levels)",
                          "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                          "frac": (achieved / peak_nominal) if achieved else None,

@@ -180,6 +180,15 @@ nrmg_status nrmg_two_grid_update(nrmg_ctx *ctx, int lf);
  * applied after each NMG step). */
 nrmg_status nrmg_mass_correct(nrmg_ctx *ctx);
 
+/* Persistent CTAs per SM of this context's sweep launches (the FP64 sweeps and the FP32
+ * correction sweeps, each capped at its kernel's occupancy); 0 restores the occupancy, the
+ * default.  Fewer resident CTAs give each cell update more of its SM's FP64 rate, more give
+ * the wavefront more look-ahead; the Python binding's autotuner times the choices.  The
+ * iteration and its results do not depend on it.  NRMG_ERR_ARG outside [0, limit], where
+ * nrmg_grid_limit returns the limit (the larger of the two kernels' occupancies). */
+nrmg_status nrmg_set_grid(nrmg_ctx *ctx, int ctas_per_sm);
+int nrmg_grid_limit(const nrmg_ctx *ctx);
+
 /* Fix the reference of the following cycles: the total mass the correction restores
  * (mass > 0; 0 keeps the current one) and the norm the relative residual divides by
  * (res0 > 0; 0 keeps the current one).  While a residual reference is fixed, nrmg_solve and

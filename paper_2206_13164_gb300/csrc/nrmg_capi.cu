@@ -326,6 +326,7 @@ struct nrmg_ctx {
   int nsm;
   int occ[4];
   int occ_corr;
+  int fs_ctas_per_sm;  // persistent CTAs per SM of the sweep launches (0: the occupancy)
   Consts K;
   LevelDev lev[kMaxLev];
   struct {
@@ -481,7 +482,9 @@ nrmg_status cuda_check(nrmg_ctx *c, cudaError_t e, const char *what) {
   } while (0)
 
 int grid_for(nrmg_ctx *ctx, int which, long long work) {
-  long long g = (long long)ctx->nsm * std::max(1, ctx->occ[which]);
+  int per_sm = std::max(1, ctx->occ[which]);
+  if (which == 0 && ctx->fs_ctas_per_sm > 0) per_sm = std::min(per_sm, ctx->fs_ctas_per_sm);
+  long long g = (long long)ctx->nsm * per_sm;
   if (work < g) g = work;
   if (g > kPartials) g = kPartials;
   return (int)std::max(1LL, g);
@@ -585,7 +588,9 @@ nrmg_status smooth_mixed(nrmg_ctx *ctx, int level, int steps) {
   const int *queue = nullptr;
   for (int q = 0; q < ctx->nsched[level]; ++q)
     if (ctx->sched[level][q].steps == steps) queue = ctx->sched[level][q].queue;
-  long long g = (long long)ctx->nsm * std::max(1, ctx->occ_corr);
+  int per_sm = std::max(1, ctx->occ_corr);
+  if (ctx->fs_ctas_per_sm > 0) per_sm = std::min(per_sm, ctx->fs_ctas_per_sm);
+  long long g = (long long)ctx->nsm * per_sm;
   g = std::min<long long>(g, (long long)steps * 4 * L.ncell);
   bool timed = ctx->profiling && ctx->ev_used + 2 <= ctx->ev.size();
   if (timed) CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
@@ -844,6 +849,14 @@ nrmg_status nrmg_set_state_from_fields(nrmg_ctx *ctx, const double *fields) {
   ctx->launches += 1;
   return finish_state(ctx, top);
 }
+
+nrmg_status nrmg_set_grid(nrmg_ctx *ctx, int ctas_per_sm) {
+  if (!ctx || ctas_per_sm < 0 || ctas_per_sm > std::max(ctx->occ[0], ctx->occ_corr)) return NRMG_ERR_ARG;
+  ctx->fs_ctas_per_sm = ctas_per_sm;
+  return NRMG_OK;
+}
+
+int nrmg_grid_limit(const nrmg_ctx *ctx) { return ctx ? std::max(1, std::max(ctx->occ[0], ctx->occ_corr)) : 0; }
 
 nrmg_status nrmg_set_reference(nrmg_ctx *ctx, double mass, double res0) {
   if (!ctx || !(mass >= 0.0) || !(res0 >= 0.0) || !isfinite(mass) || !isfinite(res0)) return NRMG_ERR_ARG;

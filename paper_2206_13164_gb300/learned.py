@@ -238,6 +238,11 @@ class LearnedSolve:
         self.res0_grid = [plain_res0(s) for s in self.main]
         self.res0 = self.res0_grid[-1]
 
+    def set_grid(self, ctas_per_sm: int):
+        """Sweep grid (persistent CTAs per SM) of every context of the solve."""
+        for s in [self.coarse] + self.main + (self.twin or []):
+            s.set_grid(min(ctas_per_sm, int(s.L.nrmg_grid_limit(s.ctx))))
+
     def run(self, tol=1e-8, coarse_tol=1e-6, polish=2, judge=2, max_cycles=400, net_grids="trained",
             polish_tol=None):
         """net_grids: the grids on which the network's candidate is built: "trained" (default) =
@@ -306,9 +311,10 @@ class LearnedSolve:
                 "judge": judge}
 
 
-def plain_solve(N, M, Kn, U, tol=1e-8, max_cycles=400, **kw):
+def plain_solve(N, M, Kn, U, tol=1e-8, max_cycles=400, grid=0, **kw):
     """The plain solve (global Maxwellian start) timed the same way: (solver, record)."""
     s = lid_solver(N, M, Kn, U, **kw)
+    s.set_grid(grid)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st, cyc, rel = s.solve(tol, max_cycles)
@@ -401,14 +407,16 @@ def train(net, data, epochs, batch=16, lr=2e-3, lr_min=2e-5, wd=1e-4, seed=0, lo
     return hist
 
 
-def evaluate(N, M, Kn, U, net, start=64, polish=2, judge=2, tol=1e-8):
+def evaluate(N, M, Kn, U, net, start=64, polish=2, judge=2, tol=1e-8, grid=0):
     """Cycles and wall time to tol on one cavity: plain start, climb without the network, climb
-    with it; the largest field difference of each against the plain solution."""
-    plain, rp = plain_solve(N, M, Kn, U, tol)
+    with it; the largest field difference of each against the plain solution.  grid: the
+    sweep grid of every context (CTAs per SM, 0 = occupancy)."""
+    plain, rp = plain_solve(N, M, Kn, U, tol, grid=grid)
     ref = plain.fields()
-    out = {"N": N, "M": M, "Kn": Kn, "U": U, "start": start, "plain": rp}
+    out = {"N": N, "M": M, "Kn": Kn, "U": U, "start": start, "grid": grid, "plain": rp}
     for name, nn in (("no_net", None), ("net", net)):
         ls = LearnedSolve(N, M, Kn, U, start=start, net=nn)
+        ls.set_grid(grid)
         r = ls.run(tol=tol, polish=polish, judge=judge)
         r["max_field_diff"] = float((ls.target.fields() - ref).abs().max())
         out[name] = r

@@ -82,6 +82,10 @@ def lib():
         L.nrmg_two_grid_update.argtypes = [c_void_p, c_int]
         L.nrmg_mass_correct.restype = c_int
         L.nrmg_mass_correct.argtypes = [c_void_p]
+        L.nrmg_set_grid.restype = c_int
+        L.nrmg_set_grid.argtypes = [c_void_p, c_int]
+        L.nrmg_grid_limit.restype = c_int
+        L.nrmg_grid_limit.argtypes = [c_void_p]
         L.nrmg_set_reference.restype = c_int
         L.nrmg_set_reference.argtypes = [c_void_p, c_double, c_double]
         L.nrmg_set_state_from_fields.restype = c_int
@@ -255,6 +259,31 @@ class Solver:
 
     def mass_correct(self):
         self._check(self.L.nrmg_mass_correct(self.ctx), "nrmg_mass_correct")
+
+    def set_grid(self, ctas_per_sm: int):
+        """Persistent CTAs per SM of the sweep launches (0: the kernel occupancy)."""
+        self._check(self.L.nrmg_set_grid(self.ctx, ctas_per_sm), "nrmg_set_grid")
+        self.tuned = ctas_per_sm
+
+    def autotune(self, candidates=None, reps=1):
+        """Time `reps` FAS cycles per candidate CTAs/SM of the sweep launches (the cycles advance
+        the solution, not its fixed point) and keep the fastest.  Returns {candidate: s/cycle}."""
+        import time
+
+        limit = int(self.L.nrmg_grid_limit(self.ctx))
+        cands = [c for c in (candidates or range(1, limit + 1)) if 1 <= c <= limit]
+        times = {}
+        for c in cands:
+            self.set_grid(c)
+            torch.cuda.synchronize(self.device)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                self.fas_cycle()
+            torch.cuda.synchronize(self.device)
+            times[c] = (time.perf_counter() - t0) / reps
+        best = min(times, key=times.get)
+        self.set_grid(best)
+        return times
 
     def set_reference(self, mass=0.0, res0=0.0):
         """Fix the reference mass of the correction and the residual norm that relative

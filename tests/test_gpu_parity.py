@@ -405,3 +405,23 @@ def test_batch_solve_matches_oracle():
         for _ in range(total - co):
             O.fas_cycle()
         compare_fields(N(S.fields()), O.fields(), 1e-10)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sweep_grid_does_not_change_results(precision):
+    """The persistent grid of the sweeps (CTAs per SM, the autotuner's knob) changes only the
+    timing: each update is still done once, in the serial order's dependencies, by one CTA."""
+    prob = lid_cavity(32, 6, 0.05, 0.3, order=2, slope=2, levels=3)
+    A = nrmg.from_problem(prob, device=DEV, precision=precision)
+    B = nrmg.from_problem(prob, device=DEV, precision=precision)
+    B.set_grid(1)
+    for _ in range(2):
+        ra, rb = A.fas_cycle(), B.fas_cycle()
+        assert ra == rb
+    Pa, Fa = A.get_state()
+    Pb, Fb = B.get_state()
+    assert torch.equal(Pa, Pb) and torch.equal(Fa, Fb)
+    limit = int(B.L.nrmg_grid_limit(B.ctx))
+    with pytest.raises(nrmg.NrmgError):
+        B.set_grid(limit + 1)
+    B.set_grid(0)
