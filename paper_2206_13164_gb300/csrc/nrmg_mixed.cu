@@ -174,22 +174,41 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     if (tid == 0) s.iarr[I_ABORT] = ld_volatile(K.abort_flag);
     __syncthreads();
     if (s.iarr[I_ABORT]) break;
-    // ---- stencil: frozen coefficients, current corrections and the FP32 state (even alpha_3)
+    // ---- stencil: frozen coefficients, current corrections and the FP32 state (even alpha_3);
+    //      each thread issues kU loads before its shared-memory stores so that they are in
+    //      flight together
     {
       const int W = 8 + 2 * NE, tot = 9 * W;
-      for (int q = tid; q < tot; q += kThreads) {
-        int sl = q / W, e = q - sl * W;
-        if (!s.iarr[I_EX + sl]) continue;
-        int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
-        if (e < 8) {
-          cstencil(s, sl, NP)[e] = __ldcg(L.aux32 + (size_t)cc * 8 + e);
-        } else if (e < 8 + NE) {
-          int o = s.eidx[e - 8];
-          cstencil(s, sl, NP)[8 + o] = __ldcg(L.e32 + (size_t)cc * NP + o);
-        } else {
-          int o = s.eidx[e - 8 - NE];
-          ss[sl * NP + o] = L.s32[(size_t)cc * NP + o];  // written before the launch
+      constexpr int kU = 8;
+      for (int q0 = tid; q0 < tot; q0 += kU * kThreads) {
+        float vv[kU];
+        float *dd[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int q = q0 + u * kThreads;
+          dd[u] = nullptr;
+          if (q < tot) {
+            const int sl = q / W, e = q - sl * W;
+            if (s.iarr[I_EX + sl]) {
+              const int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
+              if (e < 8) {
+                vv[u] = __ldcg(L.aux32 + (size_t)cc * 8 + e);
+                dd[u] = cstencil(s, sl, NP) + e;
+              } else if (e < 8 + NE) {
+                const int o = s.eidx[e - 8];
+                vv[u] = __ldcg(L.e32 + (size_t)cc * NP + o);
+                dd[u] = cstencil(s, sl, NP) + 8 + o;
+              } else {
+                const int o = s.eidx[e - 8 - NE];
+                vv[u] = L.s32[(size_t)cc * NP + o];  // written before the launch
+                dd[u] = ss + sl * NP + o;
+              }
+            }
+          }
         }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (dd[u]) *dd[u] = vv[u];
       }
     }
     if (tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
