@@ -112,12 +112,10 @@ def run_batch64(args):
     ms = e0.elapsed_time(e1)
     launches = sum(B.launches for B in batches.values()) - l0
     upd = sum(cycle_updates(w) for w in inst) * args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     if rank == 0:
-        out = {"metric": "cell-moment updates/s", "value": upd * world / (ms * 1e-3), "unit": "cell-moment updates/s",
+        out = {"metric": "cell-moment updates/s", "value": replica_throughput(upd, world, ms * 1e-3),
+               "unit": "cell-moment updates/s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": "64 lid-driven cavities (seed 0): Kn 10^U(-2,0), lid U(0.05,0.5), N in "
@@ -361,6 +359,24 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(value, device=None):
+    """Largest value over the ranks of the default process group (the value itself when there
+    is none): the job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` independent replicas: all ranks' units / the slowest time."""
+    return units_per_rank * world / seconds
+
+
 def cpu_oracle_sample(w, level_shift: int, sweeps: int = 1):
     """Time the CPU oracle (as it stands, serial) on directional sweeps D1 of one level of the
     workload.  Returns (cell-moment updates/s, seconds, description)."""
@@ -496,12 +512,9 @@ def main():
     per_level = S.fs_profile_levels()
     fs_ms, fs_n, u0, u1 = S.fs_profile()
     S.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     upd = cycle_updates(w) * args.steps
-    value = upd * world / (ms * 1e-3)
+    value = replica_throughput(upd, world, ms * 1e-3)
 
     # end to end through the public API: pinned host state -> device, one cycle, state -> host
     P, F = S.get_state()
@@ -529,11 +542,8 @@ def main():
         torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = cycle_updates(w) * e2e_steps * world / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_value = replica_throughput(cycle_updates(w) * e2e_steps, world, e2e_s)
     bytes_state = (hP.numel() + hF.numel()) * 8
 
     # mixed precision: FP32 correction sweeps inside FP64 defect correction, same cycle
