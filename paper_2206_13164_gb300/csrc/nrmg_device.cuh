@@ -61,7 +61,7 @@ using Sm = SmT<double>;
 
 // iarr slots
 enum { I_ITEM = 0, I_NACT = 1, I_ACT = 2 /* ..2+kNV */, I_EX = 16 /* ..16+9 */, I_WALL = 28 /* ..28+4 */,
-       I_BAD = 34, I_ABORT = 35 };
+       I_BAD = 34, I_ABORT = 35, I_ABW = 36 /* a dependency wait of this item gave up */ };
 // sc slots
 enum { S_DT = 0, S_NU = 1, S_Q = 2 /* ..5 */, S_W = 8 /* ..8+12: w1,w2,w3 per face */, S_RHOW = 20 /* ..24 */,
        S_NEWP = 24 /* ..28 */, S_PH = 32 /* ..36 */, S_NORM = 40, S_TPN = 42, S_RED = 44 /* ..44+8 warps */,

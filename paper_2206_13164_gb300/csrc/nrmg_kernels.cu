@@ -30,19 +30,20 @@ size_t cell_smem_bytes(int M, int NP) {
 // other CTAs have just written).  Transform vector slots: 2f / 2f+1 = face f's left / right
 // state (E, W, N, S), or 2f = the cell re-expanded in the wall basis when face f is a wall;
 // slot 8 = r.
-template <bool kCoherent, typename Emit>
+template <bool kCoherent, bool kPreloaded = false, typename Emit>
 __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, int i, int j, Emit emit) {
-  const int N = K.N, NP = K.NP, tid = threadIdx.x, W4 = 4 + NP;
+  const int N = K.N, NP = K.NP, tid = threadIdx.x;
   const int c = j * L.nx + i;
-  if (tid < 9) {
+  if (!kPreloaded && tid < 9) {
     int ii = i + c_nb_di[tid], jj = j + c_nb_dj[tid];
     int reach = abs(c_nb_di[tid]) + abs(c_nb_dj[tid]);
     s.iarr[I_EX + tid] = (ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && reach <= K.reach) ? 1 : 0;
   }
-  __syncthreads();
+  if (!kPreloaded) __syncthreads();
   // ---- stencil (params + the even-alpha_3 coefficients): each thread issues its loads
-  //      before its shared-memory stores so that they are in flight together
-  {
+  //      before its shared-memory stores so that they are in flight together (kPreloaded:
+  //      the caller has loaded the stencil and set the existence and wall flags)
+  if (!kPreloaded) {
     const int NE = K.NE, W = 4 + NE, tot = 9 * W;
     constexpr int kU = 8;
     for (int q0 = tid; q0 < tot; q0 += kU * kThreads) {
@@ -68,7 +69,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
         if (d[u]) *d[u] = v[u];
     }
   }
-  if (tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
+  if (!kPreloaded && tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
   if (L.has_r) {
     for (int e = tid; e < 4 + K.NE; e += kThreads) {
       if (e < 4) {
@@ -355,38 +356,80 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v, b
 // the versions of the serial order (the newest for a neighbour that sweep Dk visits earlier,
 // the previous one otherwise), then publish v.  Returns false when the launch must stop.
 __device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c, int k, int v) {
-  const int tid = threadIdx.x, NP = K.NP;
+  const int tid = threadIdx.x, NP = K.NP, NE = K.NE;
   const int i = c % L.nx, j = c / L.nx;
-  if (tid < 9) {
-    int di = c_nb_di[tid], dj = c_nb_dj[tid];
-    int ii = i + di, jj = j + dj;
-    int reach = abs(di) + abs(dj);
-    if (ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && reach <= K.reach) {
-      // sweep Dk: i ascending for D1, D4; j ascending for D1, D2 (outer loop i, inner j)
-      int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
-      bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
-      int need = (tid != 0 && before) ? v : v - 1;
-      const int *flag = L.ver + (size_t)jj * L.nx + ii;
-      if (ld_acquire(flag) < need) {
-        unsigned long long t0 = gtimer();
-        while (ld_acquire(flag) < need) {
-          if (ld_volatile(K.abort_flag)) break;
-          if (gtimer() - t0 > kWaitLimitNs) {
-            raise_status(K, kStTimeout, true);
-            break;
+  // ---- per stencil slot (warp w takes slot w, warp 0 also slot 8): lane 0 waits until the
+  //      cell holds the version of the serial order (sweep Dk: i ascending for D1, D4; j
+  //      ascending for D1, D2; outer loop i, inner j), then the warp loads the cell's params
+  //      and even-alpha_3 coefficients (kU loads in flight per lane).  A satisfied cell cannot
+  //      change again before this update is published, so rows that are ready early load
+  //      while the last dependency is pending.
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
+    for (int sl = warp; sl < 9; sl += kThreads / 32) {
+      const int di = c_nb_di[sl], dj = c_nb_dj[sl];
+      const int ii = i + di, jj = j + dj;
+      const bool in = ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && abs(di) + abs(dj) <= K.reach;
+      int ok = 0;
+      if (lane == 0) {
+        s.iarr[I_EX + sl] = in ? 1 : 0;
+        if (sl >= 1 && sl <= 4) s.iarr[I_WALL + sl - 1] = in ? 0 : 1;  // face f = slot f + 1
+        if (in) {
+          const bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
+          const int need = (sl != 0 && before) ? v : v - 1;
+          const int *flag = L.ver + (size_t)jj * L.nx + ii;
+          ok = 1;
+          if (ld_acquire(flag) < need) {
+            unsigned long long t0 = gtimer();
+            while (ld_acquire(flag) < need) {
+              if (ld_volatile(K.abort_flag)) {
+                ok = 0;
+                break;
+              }
+              if (gtimer() - t0 > kWaitLimitNs) {
+                raise_status(K, kStTimeout, true);
+                ok = 0;
+                break;
+              }
+              __nanosleep(32);
+            }
           }
-          __nanosleep(32);
+          if (!ok) s.iarr[I_ABW] = 1;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (ok) {
+        const int cc = c + dj * L.nx + di;
+        double *row = stencil(s, sl, NP);
+        const int W = 4 + NE;
+        constexpr int kU = 8;
+        for (int q0 = lane; q0 < W; q0 += kU * 32) {
+          double vv[kU];
+          double *dd[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int e = q0 + u * 32;
+            dd[u] = nullptr;
+            if (e < W) {
+              const int col = e < 4 ? e : 4 + s.eidx[e - 4];
+              const double *ptr = e < 4 ? L.P + (size_t)cc * 4 + e : L.F + (size_t)cc * NP + (col - 4);
+              vv[u] = __ldcg(ptr);
+              dd[u] = row + col;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u)
+            if (dd[u]) *dd[u] = vv[u];
         }
       }
     }
   }
   __syncthreads();
-  if (tid == 0) s.iarr[I_ABORT] = ld_volatile(K.abort_flag);
-  __syncthreads();
-  if (s.iarr[I_ABORT]) return false;
+  if (s.iarr[I_ABW]) return false;
   // ---- R_ij(f) - r_ij, then f + dt (R - r) into VA slot 4, back to Grad form
-  cell_residual<true>(K, L, s, i, j,
-                      [&](int o, double Rr) { s.VA[4 * NP + o] = fma(s.sc[S_DT], Rr, s.cst[4 + o]); });
+  cell_residual<true, true>(K, L, s, i, j,
+                            [&](int o, double Rr) { s.VA[4 * NP + o] = fma(s.sc[S_DT], Rr, s.cst[4 + o]); });
   __syncthreads();
   double pcell[4];
   for (int e = 0; e < 4; ++e) pcell[e] = s.cst[e];
@@ -420,6 +463,7 @@ __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int 
       int it = atomicAdd(K.queue, 1);
       if (ld_volatile(K.abort_flag)) it = (int)total;
       s.iarr[I_ITEM] = it;
+      s.iarr[I_ABW] = 0;
     }
     __syncthreads();
     const long long item = s.iarr[I_ITEM];
@@ -456,6 +500,7 @@ __global__ void __launch_bounds__(kThreads) fs_batch_kernel(const BatchDesc *des
       int it = atomicAdd(counter, 1);
       if (ld_volatile(K0.abort_flag)) it = (int)total;
       s.iarr[I_ITEM] = it;
+      s.iarr[I_ABW] = 0;
     }
     __syncthreads();
     const long long item = s.iarr[I_ITEM];

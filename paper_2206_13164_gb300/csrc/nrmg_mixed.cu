@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       int it = atomicAdd(K.queue, 1);
       if (ld_volatile(K.abort_flag)) it = (int)total;
       s.iarr[I_ITEM] = it;
+      s.iarr[I_ABW] = 0;
     }
     __syncthreads();
     const long long item = s.iarr[I_ITEM];
@@ -146,73 +147,81 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     }
     const int i = c % L.nx, j = c / L.nx;
     const int v = 4 * st + k + 1;
-    // ---- cross stencil of the scheme's reach: wait for the versions of the serial order
-    if (tid < 9) {
-      int di = c_nb_di[tid], dj = c_nb_dj[tid];
-      int ii = i + di, jj = j + dj;
-      bool in = ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && abs(di) + abs(dj) <= K.reach;
-      s.iarr[I_EX + tid] = in ? 1 : 0;
-      if (in) {
-        int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
-        bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
-        int need = (tid != 0 && before) ? v : v - 1;
-        const int *flag = L.ver + (size_t)jj * L.nx + ii;
-        if (ld_acquire(flag) < need) {
-          unsigned long long t0 = gtimer();
-          while (ld_acquire(flag) < need) {
-            if (ld_volatile(K.abort_flag)) break;
-            if (gtimer() - t0 > kWaitLimitNs) {
-              raise_status(K, kStTimeout, true);
-              break;
+    // ---- per stencil slot (warp w takes slot w, warp 0 also slot 8): lane 0 waits until the
+    //      cell holds the version of the serial order (the newest for a neighbour that sweep Dk
+    //      visits earlier, the previous one otherwise), then the warp loads the cell's row:
+    //      frozen coefficients, correction and FP32 state (even alpha_3 entries, kU loads in
+    //      flight per lane).  A satisfied cell cannot change again before this update is
+    //      published, so rows that are ready early load while the last dependency is pending.
+    {
+      const int warp = tid >> 5, lane = tid & 31;
+      const int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
+      for (int sl = warp; sl < 9; sl += kThreads / 32) {
+        const int di = c_nb_di[sl], dj = c_nb_dj[sl];
+        const int ii = i + di, jj = j + dj;
+        const bool in = ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && abs(di) + abs(dj) <= K.reach;
+        int ok = 0;
+        if (lane == 0) {
+          s.iarr[I_EX + sl] = in ? 1 : 0;
+          if (sl >= 1 && sl <= 4) s.iarr[I_WALL + sl - 1] = in ? 0 : 1;  // face f = slot f + 1
+          if (in) {
+            const bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
+            const int need = (sl != 0 && before) ? v : v - 1;
+            const int *flag = L.ver + (size_t)jj * L.nx + ii;
+            ok = 1;
+            if (ld_acquire(flag) < need) {
+              unsigned long long t0 = gtimer();
+              while (ld_acquire(flag) < need) {
+                if (ld_volatile(K.abort_flag)) {
+                  ok = 0;
+                  break;
+                }
+                if (gtimer() - t0 > kWaitLimitNs) {
+                  raise_status(K, kStTimeout, true);
+                  ok = 0;
+                  break;
+                }
+                __nanosleep(32);
+              }
             }
-            __nanosleep(32);
+            if (!ok) s.iarr[I_ABW] = 1;
           }
         }
-      }
-    }
-    __syncthreads();
-    if (tid == 0) s.iarr[I_ABORT] = ld_volatile(K.abort_flag);
-    __syncthreads();
-    if (s.iarr[I_ABORT]) break;
-    // ---- stencil: frozen coefficients, current corrections and the FP32 state (even alpha_3);
-    //      each thread issues kU loads before its shared-memory stores so that they are in
-    //      flight together
-    {
-      const int W = 8 + 2 * NE, tot = 9 * W;
-      constexpr int kU = 8;
-      for (int q0 = tid; q0 < tot; q0 += kU * kThreads) {
-        float vv[kU];
-        float *dd[kU];
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) {
+          const int cc = c + dj * L.nx + di;
+          float *row = cstencil(s, sl, NP), *srow = ss + sl * NP;
+          const int W = 8 + 2 * NE;
+          constexpr int kU = 8;
+          for (int q0 = lane; q0 < W; q0 += kU * 32) {
+            float vv[kU];
+            float *dd[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int q = q0 + u * kThreads;
-          dd[u] = nullptr;
-          if (q < tot) {
-            const int sl = q / W, e = q - sl * W;
-            if (s.iarr[I_EX + sl]) {
-              const int cc = c + c_nb_dj[sl] * L.nx + c_nb_di[sl];
+            for (int u = 0; u < kU; ++u) {
+              const int e = q0 + u * 32;
+              dd[u] = nullptr;
               if (e < 8) {
                 vv[u] = __ldcg(L.aux32 + (size_t)cc * 8 + e);
-                dd[u] = cstencil(s, sl, NP) + e;
+                dd[u] = row + e;
               } else if (e < 8 + NE) {
                 const int o = s.eidx[e - 8];
                 vv[u] = __ldcg(L.e32 + (size_t)cc * NP + o);
-                dd[u] = cstencil(s, sl, NP) + 8 + o;
-              } else {
+                dd[u] = row + 8 + o;
+              } else if (e < W) {
                 const int o = s.eidx[e - 8 - NE];
                 vv[u] = L.s32[(size_t)cc * NP + o];  // written before the launch
-                dd[u] = ss + sl * NP + o;
+                dd[u] = srow + o;
               }
             }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+              if (dd[u]) *dd[u] = vv[u];
           }
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-          if (dd[u]) *dd[u] = vv[u];
       }
     }
-    if (tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
     __syncthreads();
+    if (s.iarr[I_ABW]) break;
     const float *ac = s.cst, *ec = s.cst + 8;  // own frozen coefficients, own correction
     // ---- face states of the correction, slots as in the FP64 operator: 2f / 2f+1 = face f's
     //      left / right state (E, W, N, S), or 2f = the cell in the wall basis at a wall
