@@ -174,16 +174,20 @@ __device__ inline void setup_coeffs(const Consts &K, SmT<T> &s) {
 // non-vanishing k, split over two accumulators so that two FMA chains run side by side
 template <typename T>
 __device__ inline T transform_one(const T *x, const T *c, const uint16_t *mem, int o, int s0, int p, int fl) {
-  T a0 = x[o], a1 = T(0);
-  if (!(fl & 1)) {
-    const int st = (fl & 2) ? 2 : 1;
-    int k = st;
-    for (; k + st <= p; k += 2 * st) {
-      a0 = fma(c[k], x[mem[s0 - k]], a0);
-      a1 = fma(c[k + st], x[mem[s0 - k - st]], a1);
-    }
-    if (k <= p) a0 = fma(c[k], x[mem[s0 - k]], a0);
+  T a0 = x[o];
+  if (fl & 1) return a0;
+  const int st = (fl & 2) ? 2 : 1;
+  if (p < 2 * st) {  // at most one term: one chain, no closing add (the FP64 pipe is the bound)
+    if (st <= p) a0 = fma(c[st], x[mem[s0 - st]], a0);
+    return a0;
   }
+  T a1 = T(0);
+  int k = st;
+  for (; k + st <= p; k += 2 * st) {
+    a0 = fma(c[k], x[mem[s0 - k]], a0);
+    a1 = fma(c[k + st], x[mem[s0 - k - st]], a1);
+  }
+  if (k <= p) a0 = fma(c[k], x[mem[s0 - k]], a0);
   return a0 + a1;
 }
 

@@ -442,11 +442,10 @@ __device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c,
   if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
   if (tid == 4) L.tp[c] = s.sc[S_TPN];
   if (!ok && tid == 0) raise_status(K, kStNonPhysical, true);
+  // the barrier orders every thread's writes of the cell before thread 0's release store
+  // (gpu scope), which the dependants' acquire loads synchronize with
   __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    st_release(L.ver + c, v);
-  }
+  if (tid == 0) st_release(L.ver + c, v);
   return true;
 }
 

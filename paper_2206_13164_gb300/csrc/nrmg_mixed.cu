@@ -428,11 +428,8 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       float R = fmaf(-(xi[0] + eX[o]), idx, fmaf(-(xi[1] + eY[o]), idy, nu * (pe - ec[o])));
       Eo[o] = fmaf(dt, R - Do[o], ec[o]);
     }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      st_release(L.ver + c, v);
-    }
+    __syncthreads();  // orders the correction's writes before the release store
+    if (tid == 0) st_release(L.ver + c, v);
   }
 }
 
