@@ -248,7 +248,7 @@ nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, double Kn, const
                                   const double *dev_coeffs, double *dev_R_out, double *norm_out,
                                   void *cuda_stream);
 
-/* Batches (BASELINE's batched form; the paper solves one cavity at a time).  A batch runs
+/* Batches (the paper solves one cavity at a time; this is the batched form).  A batch runs
  * the V-cycles of several contexts in lockstep, aligned by depth below each context's finest
  * level: every FS stage of all problems (pre-smoothing at one depth together with the
  * coarsest solves reached there, or post-smoothing at one depth) is ONE persistent launch
