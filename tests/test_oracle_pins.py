@@ -577,9 +577,9 @@ def test_fas_iterations_match_the_papers_table():
     from inputs import levels_to_8
 
     here = os.path.dirname(os.path.abspath(__file__))
-    rows = [l.split() for l in open(os.path.join(here, "golden", "paper_table1_nmg_iterations.txt"))
+    rows = [l.split() for l in open(os.path.join(here, "golden", "paper_iteration_counts.txt"))
             if l.strip() and not l.startswith("#")]
-    paper = {int(a): int(b) for a, b in rows}
+    paper = {int(r[6]): int(r[8]) for r in rows if r[0] == "Table1" and r[7] == "NMG"}
     U = 50.0 / math.sqrt(208.13 * 273.0)
     got = {}
     for N in (32, 64):
