@@ -236,7 +236,7 @@ def run_learned512(args):
     grid = tuner.tuned
     del tuner
     with ClockSampler(gpu_id) as clk:
-        ev = learned.evaluate(N, M, Kn, U, net, start=64, grid=grid)
+        ev = learned.evaluate(N, M, Kn, U, net, start=64, grid=grid, mixed=True)
     peak, src = bf16_peak()
     t_net, t_plain = ev["net"]["t_total"], ev["plain"]["t_total"]
     out = {"metric": "seconds to relative residual 1e-8 (learned start)", "value": t_net, "unit": "s",
@@ -251,7 +251,11 @@ def run_learned512(args):
            "plain": {k: ev["plain"][k] for k in ("status", "cycles", "rel_res", "t_total")},
            "no_net": {k: ev["no_net"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
            "net": {k: ev["net"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
+           "plain_mixed": {k: ev["plain_mixed"][k] for k in ("status", "cycles", "rel_res", "t_total",
+                                                             "max_field_diff")},
+           "net_mixed": {k: ev["net_mixed"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
            "speedup_vs_plain": t_plain / t_net,
+           "speedup_vs_plain_with_mixed_smoother": t_plain / ev["net_mixed"]["t_total"],
            "roofline": {"bound": "tensor", "kernel": "network forward (4 conv3x3 launches, mma.sync BF16)",
                         "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,
                         "traffic": None, "peak_source": src, "forward_ms": fwd_ms,

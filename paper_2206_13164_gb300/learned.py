@@ -407,15 +407,22 @@ def train(net, data, epochs, batch=16, lr=2e-3, lr_min=2e-5, wd=1e-4, seed=0, lo
     return hist
 
 
-def evaluate(N, M, Kn, U, net, start=64, polish=2, judge=2, tol=1e-8, grid=0):
+def evaluate(N, M, Kn, U, net, start=64, polish=2, judge=2, tol=1e-8, grid=0, mixed=False):
     """Cycles and wall time to tol on one cavity: plain start, climb without the network, climb
-    with it; the largest field difference of each against the plain solution.  grid: the
-    sweep grid of every context (CTAs per SM, 0 = occupancy)."""
+    with it (and, with mixed, the plain start and the climb with the network on the
+    mixed-precision smoother); the largest field difference of each against the plain
+    solution.  grid: the sweep grid of every context (CTAs per SM, 0 = occupancy)."""
     plain, rp = plain_solve(N, M, Kn, U, tol, grid=grid)
     ref = plain.fields()
     out = {"N": N, "M": M, "Kn": Kn, "U": U, "start": start, "grid": grid, "plain": rp}
-    for name, nn in (("no_net", None), ("net", net)):
-        ls = LearnedSolve(N, M, Kn, U, start=start, net=nn)
+    if mixed:
+        pm, rpm = plain_solve(N, M, Kn, U, tol, grid=grid, precision=1)
+        rpm["max_field_diff"] = float((pm.fields() - ref).abs().max())
+        out["plain_mixed"] = rpm
+        pm.close()
+    runs = [("no_net", None, 0), ("net", net, 0)] + ([("net_mixed", net, 1)] if mixed else [])
+    for name, nn, prec in runs:
+        ls = LearnedSolve(N, M, Kn, U, start=start, net=nn, precision=prec)
         ls.set_grid(grid)
         r = ls.run(tol=tol, polish=polish, judge=judge)
         r["max_field_diff"] = float((ls.target.fields() - ref).abs().max())
