@@ -53,6 +53,8 @@ CASES = [
     ("lid_M8_o2va_10", lid_cavity(10, 8, 0.01, 0.5, order=2, slope=2), 0.03),
     ("lid_M10_o2va_8", lid_cavity(8, 10, 0.01, 0.5, order=2, slope=2), 0.03),
     ("lid_dtnu_M4_12", lid_cavity(12, 4, 0.02, 0.4, order=2, slope=2, dtnu=0.5), 0.05),
+    ("lid_M16_o2va_6x5", lid_cavity(6, 16, 0.05, 0.3, order=2, slope=2).replace(ny=5), 0.02),  # largest M
+    ("heat_M13_o1_7", heated_cavity(7, 13, 0.2, order=1), 0.02),
     ("partial_wall_chi", lid_cavity(9, 4, 0.1, 0.3, order=2, slope=2).replace(
         walls=[w.__class__(u=w.u, theta=w.theta, chi=0.6) for w in lid_cavity(9, 4, 0.1, 0.3).walls]), 0.05),
 ]
