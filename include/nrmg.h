@@ -74,11 +74,14 @@ typedef struct {
   double chi;
 } nrmg_wall;
 
-typedef enum { NRMG_BGK = 0, NRMG_SHAKHOV = 1 } nrmg_model;
+typedef enum { NRMG_BGK = 0, NRMG_SHAKHOV = 1, NRMG_ESBGK = 2 } nrmg_model;
 
 /* Collision frequency nu = beta sqrt(pi/2) rho theta^(1-omega) / Kn
- * (Sec. 4, eq. nu-shakhov); Pr is used by the Shakhov model
- * (eq. Shakhov-f^E); Shakhov with Pr = 1 is BGK (Sec. 2.1). */
+ * (Sec. 4, eq. nu-shakhov; the paper takes beta = 1 for Shakhov and
+ * beta = Pr for ES-BGK).  Pr is used by the Shakhov model (eq. Shakhov-f^E)
+ * and the ES-BGK model (eq. ES-f^E, the Gaussian of covariance
+ * Lambda = theta I + (1 - 1/Pr) sigma / rho, expanded in the cell's basis up
+ * to degree M); either with Pr = 1 is BGK (Sec. 2.1). */
 typedef struct {
   int model; /* nrmg_model */
   double Pr, omega, beta;
@@ -94,11 +97,14 @@ typedef struct {
  *   precision: 0 = FP64 throughout; 1 = mixed: on every level above the
  *     coarsest, each FS^s of Algorithm 2 becomes one FP64 defect evaluation
  *     d = r - R(f), s FP32 Gauss-Seidel steps (same cell order) on a
- *     frozen-coefficient first-order linearization L e = d for the correction
- *     e, and the FP64 update f <- Grad(f + e); the residual, the transfers, the
- *     coarsest solve and the convergence test stay FP64, so the iteration
- *     converges to the same FP64 fixed point R(f) = r.  nrmg_smooth always runs
- *     the FP64 Algorithm 1. */
+ *     linearization L e = d for the correction e (frozen cell bases, time steps
+ *     and collision frequencies; the reconstruction of the same order with the
+ *     limiter's weights frozen at f), and the FP64 update f <- Grad(f + e); the
+ *     residual, the transfers, the coarsest solve and the convergence test stay
+ *     FP64, so the iteration converges to the same FP64 fixed point R(f) = r.
+ *     Where the frozen limiter weights make the mixed cycle stall (see
+ *     nrmg_solve), nrmg_solve finishes with FP64 smoothing.  nrmg_smooth always
+ *     runs the FP64 Algorithm 1. */
 typedef struct {
   int order, slope;
   double cfl;
@@ -161,8 +167,15 @@ nrmg_status nrmg_residual(nrmg_ctx *ctx, int level, double *dev_R_out, double *n
 nrmg_status nrmg_fas_cycle(nrmg_ctx *ctx, double *rel_res_out);
 
 /* Cycles until ||R(f)|| / ||R(f^0)|| <= tol (eq. relative-residual) or
- * max_cycles.  NRMG_ERR_NOT_CONVERGED when tol was not reached. */
+ * max_cycles.  NRMG_ERR_NOT_CONVERGED when tol was not reached.
+ * precision 1: when the smallest relative residual seen has fallen by less than
+ * a factor 0.8 over the last 8 cycles, the remaining cycles of this call smooth
+ * in FP64 (nrmg_mixed_fallback then returns 1); each call starts mixed. */
 nrmg_status nrmg_solve(nrmg_ctx *ctx, double tol, int max_cycles, int *cycles_out, double *rel_res_out);
+
+/* 1 when the last nrmg_solve of a precision-1 context switched to FP64
+ * smoothing because the mixed cycle stalled, else 0 (also for a NULL ctx). */
+int nrmg_mixed_fallback(const nrmg_ctx *ctx);
 
 /* Macroscopic fields of the finest level (eq. moments-relation) into
  * dev_out [cells][14]: rho, u1, u2, u3, theta, s11, s12, s13, s22, s23, s33,

@@ -24,7 +24,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 OK, ERR_ARG, ERR_NONPHYSICAL, ERR_NOT_CONVERGED = 0, 1, 4, 5
-BGK, SHAKHOV = 0, 1
+BGK, SHAKHOV, ESBGK = 0, 1, 2
 
 
 def build(force: bool = False) -> str:

@@ -16,8 +16,9 @@
  *   - basis transformation F_M^[w,t] -> F_M^[w~,t~] Sec. 2.3 (projection of fluxes)
  *   - finite-volume residual R_ij ................. Sec. 2.3, eq. (ode-system),
  *                                                  eq. (flux-force-expansion), eq. (moments-recon)
- *   - BGK / Shakhov collision ..................... Sec. 2.1, eq. (col-relaxation),
- *                                                  eq. (BGK-f^E), eq. (Shakhov-f^E); Sec. 4, eq. (nu-shakhov)
+ *   - BGK / Shakhov / ES-BGK collision ............ Sec. 2.1, eq. (col-relaxation),
+ *                                                  eq. (BGK-f^E), eq. (Shakhov-f^E), eq. (ES-f^E);
+ *                                                  Sec. 4, eq. (nu-shakhov)
  *   - local time step, two-step update ............ Sec. 2.4, eq. (local-CFL)
  *   - fast sweeping step FS(f, r) ................. Sec. 3.1, Algorithm 1
  *   - restriction / prolongation .................. Sec. 3.2.2, eq. (uH-thetaH-computation),
@@ -54,7 +55,7 @@
 #define OR_MAXLEV 16
 
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_NONPHYSICAL = 4, OR_ERR_NOT_CONVERGED = 5 };
-enum { OR_BGK = 0, OR_SHAKHOV = 1 };
+enum { OR_BGK = 0, OR_SHAKHOV = 1, OR_ESBGK = 2 };
 
 /* van Albada smoothing constant (squared), nondimensional */
 #define OR_VA_EPS2 1e-12
@@ -564,7 +565,56 @@ void or_wall_flux(int M, const double *uw, double thw, double chi, int w, const 
 /* with v = (xi-u)/sqrt(theta), v_i(|v|^2-5) = He_3(v_i) +             */
 /* sum_{d!=i} He_1(v_i) He_2(v_d), so f^E has coefficient              */
 /* (1-Pr) q_i / 5 at 3e_i and at e_i + 2e_d (d != i), besides rho at 0. */
+/* ES-BGK (eq. ES-f^E): f^E is the Gaussian of covariance Lambda.  In   */
+/* the variable v the generating function sum_alpha He_alpha(v)        */
+/* t^alpha / alpha! = exp(t.v - |t|^2/2) has, under that Gaussian, the */
+/* mean exp(t^T (Lambda/theta - I) t / 2); with the coefficient        */
+/* formula f_alpha = theta^{|alpha|/2}/alpha! int He_alpha(v) f dxi    */
+/* this gives f^E_alpha = rho [s^alpha] exp(s^T B s / 2), where        */
+/* B = Lambda - theta I = (1 - 1/Pr) sigma / rho and sigma_ij =        */
+/* (1 + delta_ij) f_{e_i+e_j} (eq. moments-relation).  The exponential  */
+/* is summed as its power series, truncated at degree M.               */
 /* ------------------------------------------------------------------ */
+static void esbgk_equilibrium(const basis_t *b, double Pr, const double *f, double *fE) {
+  int n = b->n, M = b->M;
+  double rho = f[0];
+  /* q(s) = s^T B s / 2 as coefficients of the monomials s_i s_j, i <= j */
+  double qc[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      int t[3] = {0, 0, 0};
+      t[i] += 1;
+      t[j] += 1;
+      double sigma = (i == j ? 2.0 : 1.0) * f[idx3(b, t[0], t[1], t[2])];
+      double Bij = (1.0 - 1.0 / Pr) * sigma / rho;
+      qc[i][j] = (i == j) ? 0.5 * Bij : Bij;
+    }
+  double term[OR_MAXN], next[OR_MAXN];
+  for (int o = 0; o < n; ++o) term[o] = fE[o] = 0.0;
+  term[0] = 1.0;
+  fE[0] = 1.0;
+  /* term_k = q^k / k!, from term_{k-1} * q / k */
+  for (int k = 1; 2 * k <= M; ++k) {
+    for (int o = 0; o < n; ++o) {
+      double acc = 0.0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+          int t[3] = {b->a[o][0], b->a[o][1], b->a[o][2]};
+          t[i] -= 1;
+          t[j] -= 1;
+          int p = idx3(b, t[0], t[1], t[2]);
+          if (p >= 0) acc += qc[i][j] * term[p];
+        }
+      next[o] = acc / k;
+    }
+    for (int o = 0; o < n; ++o) {
+      term[o] = next[o];
+      fE[o] += term[o];
+    }
+  }
+  for (int o = 0; o < n; ++o) fE[o] *= rho;
+}
+
 void or_collision(int M, int model, double Kn, double Pr, double omega, double beta, const double *pc,
                   const double *f, double *Q) {
   const basis_t *b = basis(M);
@@ -594,6 +644,8 @@ void or_collision(int M, int model, double Kn, double Pr, double omega, double b
         fE[idx3(b, t[0], t[1], t[2])] = (1.0 - Pr) * q / 5.0;
       }
     }
+  } else if (model == OR_ESBGK) {
+    esbgk_equilibrium(b, Pr, f, fE);
   }
   for (int o = 0; o < n; ++o) Q[o] = nu * (fE[o] - f[o]);
 }

@@ -341,6 +341,8 @@ struct nrmg_ctx {
   double m0, res0;
   int have_res0;
   int ref_fixed;              // res0 set by nrmg_set_reference: solves keep it
+  int mixed_off;              // precision 1: FP64 smoothing for the rest of this solve (stall)
+  int mixed_stalled;          // the last nrmg_solve switched to FP64 smoothing
   long long launches;
   // event timing of FS launches
   int profiling;
@@ -609,7 +611,7 @@ nrmg_status smooth_mixed(nrmg_ctx *ctx, int level, int steps) {
 }
 
 nrmg_status smooth_level(nrmg_ctx *ctx, int level, int steps) {
-  if (ctx->opts.precision == 1 && level > 0) return smooth_mixed(ctx, level, steps);
+  if (ctx->opts.precision == 1 && !ctx->mixed_off && level > 0) return smooth_mixed(ctx, level, steps);
   return smooth(ctx, level, steps);
 }
 
@@ -679,7 +681,7 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
   *out = nullptr;
   if (!grid_ok(grid) || M < 3 || M > kMaxM || !(Kn > 0.0) || !walls || !coll || !opts_ok(opts) || !dev_workspace)
     return NRMG_ERR_ARG;
-  if (coll->model != NRMG_BGK && coll->model != NRMG_SHAKHOV) return NRMG_ERR_ARG;
+  if (coll->model != NRMG_BGK && coll->model != NRMG_SHAKHOV && coll->model != NRMG_ESBGK) return NRMG_ERR_ARG;
   if (!(coll->beta > 0.0) || !(coll->Pr > 0.0) || !isfinite(coll->omega)) return NRMG_ERR_ARG;
   for (int w = 0; w < 4; ++w) {
     if (!(walls[w].theta > 0.0) || walls[w].chi < 0.0 || walls[w].chi > 1.0) return NRMG_ERR_ARG;
@@ -940,16 +942,31 @@ nrmg_status nrmg_solve(nrmg_ctx *ctx, double tol, int max_cycles, int *cycles_ou
     ctx->have_res0 = 1;
     rr = ctx->res0 > 0.0 ? 1.0 : 0.0;
   }
+  // precision 1: stall test on the running minimum of the relative residual
+  constexpr int kStallWindow = 8;
+  constexpr double kStallDrop = 0.8;
+  double best[kStallWindow + 1];
+  ctx->mixed_off = 0;
+  ctx->mixed_stalled = 0;
   int it = 0;
   while (rr > tol && it < max_cycles) {
     if ((s = nrmg_fas_cycle(ctx, &rr)) != NRMG_OK) break;
     ++it;
+    if (ctx->opts.precision == 1 && !ctx->mixed_off) {
+      const double b = it == 1 ? rr : std::min(rr, best[(it - 1) % (kStallWindow + 1)]);
+      if (it > kStallWindow && b > kStallDrop * best[(it - kStallWindow) % (kStallWindow + 1)]) ctx->mixed_off = 1;
+      best[it % (kStallWindow + 1)] = b;
+    }
   }
+  ctx->mixed_stalled = ctx->mixed_off;
+  ctx->mixed_off = 0;
   if (cycles_out) *cycles_out = it;
   if (rel_res_out) *rel_res_out = rr;
   if (s == NRMG_OK && rr > tol) s = NRMG_ERR_NOT_CONVERGED;
   return s;
 }
+
+int nrmg_mixed_fallback(const nrmg_ctx *ctx) { return ctx ? ctx->mixed_stalled : 0; }
 
 nrmg_status nrmg_fields(nrmg_ctx *ctx, double *dev_out) {
   if (!ctx || !dev_out) return NRMG_ERR_ARG;
@@ -1455,7 +1472,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   if (!grid_ok(grid) || M < 3 || M > kMaxM || !(Kn > 0.0) || !walls || !coll || !opts_ok(opts) || !dev_params ||
       !dev_coeffs)
     return NRMG_ERR_ARG;
-  if (coll->model != NRMG_BGK && coll->model != NRMG_SHAKHOV) return NRMG_ERR_ARG;
+  if (coll->model != NRMG_BGK && coll->model != NRMG_SHAKHOV && coll->model != NRMG_ESBGK) return NRMG_ERR_ARG;
   if (!(coll->beta > 0.0) || !(coll->Pr > 0.0) || !isfinite(coll->omega)) return NRMG_ERR_ARG;
   for (int w = 0; w < 4; ++w) {
     if (!(walls[w].theta > 0.0) || walls[w].chi < 0.0 || walls[w].chi > 1.0) return NRMG_ERR_ARG;

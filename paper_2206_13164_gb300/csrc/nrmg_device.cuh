@@ -65,7 +65,10 @@ enum { I_ITEM = 0, I_NACT = 1, I_ACT = 2 /* ..2+kNV */, I_EX = 16 /* ..16+9 */, 
 // sc slots
 enum { S_DT = 0, S_NU = 1, S_Q = 2 /* ..5 */, S_W = 8 /* ..8+12: w1,w2,w3 per face */, S_RHOW = 20 /* ..24 */,
        S_NEWP = 24 /* ..28 */, S_PH = 32 /* ..36 */, S_NORM = 40, S_TPN = 42, S_RED = 44 /* ..44+8 warps */,
-       S_TPOW = 64 /* ..64+kMaxM+1: theta^-k */ };
+       S_TPOW = 64 /* ..64+kMaxM+1: theta^-k */,
+       // ES-BGK equilibrium factors: (B_dd/2)^m/m! for d = 1..3, m <= kMaxM/2, and B_12^k/k!
+       S_ESG = 82 /* ..82+3*(kMaxM/2+1) */, S_ESH = 110 /* ..110+kMaxM+1 */ };
+static_assert(S_ESH + kMaxM + 1 <= kScal && S_TPOW + kMaxM + 1 <= S_ESG, "per-cell scalar slots overlap");
 
 constexpr uint16_t kNone = 0xFFFF;
 

@@ -16,6 +16,8 @@
 // records NRMG_ERR_TIMEOUT and all CTAs leave.
 #include "nrmg_device.cuh"
 
+#include <algorithm>
+
 namespace nrmg {
 
 size_t cell_smem_bytes(int M, int NP) {
@@ -24,13 +26,57 @@ size_t cell_smem_bytes(int M, int NP) {
 }
 
 // ------------------------------------------------------------------ the cell operator
+// ES-BGK (eq. ES-f^E): B = Lambda - theta I = (1 - 1/Pr) sigma / rho with sigma_dd = 2 f_{2e_d},
+// sigma_12 = f_{e1+e2}; a planar state has sigma_13 = sigma_23 = 0, so exp(s^T B s / 2) factors
+// into exp(B_dd s_d^2 / 2) (d = 1..3) and exp(B_12 s_1 s_2).  Threads 96..99 tabulate the factors'
+// Taylor coefficients.
+__device__ inline void es_factors(const int *is, double Pr, int M, const double *f, double *sc) {
+  const int tid = threadIdx.x;
+  if (tid < 96 || tid >= 100) return;
+  const double kb = (1.0 - 1.0 / Pr) / f[0];
+  if (tid < 99) {
+    const int d = tid - 96;
+    const double half_b = kb * f[is[d == 0 ? 0 : (d == 1 ? 3 : 5)]];  // B_dd / 2
+    double t = 1.0;
+    for (int m = 0; 2 * m <= M; ++m) {
+      sc[S_ESG + d * (kMaxM / 2 + 1) + m] = t;
+      t *= half_b / (m + 1);
+    }
+  } else {
+    const double b12 = kb * f[is[1]];
+    double t = 1.0;
+    for (int k = 0; k <= M; ++k) {
+      sc[S_ESH + k] = t;
+      t *= b12 / (k + 1);
+    }
+  }
+}
+
+// f^E_alpha = rho [s^alpha] exp(s^T B s / 2) = rho g3(a3) sum_k B_12^k/k! g1(a1 - k) g2(a2 - k),
+// gd(n) = (B_dd/2)^(n/2) / (n/2)! for even n and 0 for odd n; written to out[o] for every
+// moment with even alpha_3 (eidx); tal holds alpha_1, alpha_2, alpha_3 of each moment.
+__device__ inline void es_equilibrium(int N, int NE, const uint16_t *eidx, const uint16_t *tal,
+                                            const double *sc, double rho, double *out) {
+  const double *g = sc + S_ESG, *h = sc + S_ESH;
+  for (int q = threadIdx.x; q < NE; q += kThreads) {
+    const int o = eidx[q];
+    const int a1 = tal[o], a2 = tal[N + o], a3 = tal[2 * N + o];
+    double acc = 0.0;
+    if (!((a1 ^ a2) & 1))
+      for (int k = a1 & 1; k <= min(a1, a2); k += 2)
+        acc = fma(h[k] * g[(a1 - k) >> 1], g[(kMaxM / 2 + 1) + ((a2 - k) >> 1)], acc);
+    out[o] = rho * acc * g[2 * (kMaxM / 2 + 1) + (a3 >> 1)];
+  }
+}
+
 // Loads the stencil of cell c (i,j) and computes, per coefficient, R_ij(f) - r_ij
 // (eq. ode-system in the cell basis).  Threads receive elements o = tid, tid + kThreads, ...
 // through emit(o, R_o - r_o).  kCoherent selects L2-only loads (the sweep kernel reads cells
 // other CTAs have just written).  Transform vector slots: 2f / 2f+1 = face f's left / right
 // state (E, W, N, S), or 2f = the cell re-expanded in the wall basis when face f is a wall;
 // slot 8 = r.
-template <bool kCoherent, bool kPreloaded = false, typename Emit>
+// kES: the ES-BGK instantiation (model 2); the other models' instantiation carries no ES code.
+template <bool kCoherent, bool kPreloaded = false, bool kES = false, typename Emit>
 __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, int i, int j, Emit emit) {
   const int N = K.N, NP = K.NP, tid = threadIdx.x;
   const int c = j * L.nx + i;
@@ -174,6 +220,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     for (int d = 0; d < 3; ++d) q += f[iq[1 + d]];
     s.sc[S_Q + ii] = q;
   }
+  if (kES) es_factors(K.tab_i32 + K.iq_off + 12, K.Pr, K.M, pc + 4, s.sc);
   __syncthreads();
   // ---- HLL weights per interior face: F = w1 Xi a- + w2 Xi a+ + w3 (a+ - a-)
   // (on warp 1, in parallel with warp 0's coefficient recurrences)
@@ -273,6 +320,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     eX[o] = ee[0];
     eY[o] = ee[1];
   }
+  if (kES) es_equilibrium(N, NE, s.eidx, s.tal, s.sc, pc[4], s.VA + 5 * NP);
   __syncthreads();
   // ---- R = -(F_E - F_W)/dx - (F_N - F_S)/dy + Q
   const double *f = pc + 4;
@@ -295,6 +343,8 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     } else if (K.model == 1) {
       int t = s.tshak[o];
       if (t >= 0) fE = (1.0 - K.Pr) * s.sc[S_Q + t] * 0.2;
+    } else if (kES) {
+      fE = s.VA[5 * NP + o];
     }
     double Q = nu * (fE - f[o]);
     double R = fma(-(xi[0] + eX[o]), L.idx, fma(-(xi[1] + eY[o]), L.idy, Q));
@@ -355,6 +405,7 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v, b
 // One sweep item: update cell c (i,j) of sweep k to version v once the cross stencil holds
 // the versions of the serial order (the newest for a neighbour that sweep Dk visits earlier,
 // the previous one otherwise), then publish v.  Returns false when the launch must stop.
+template <bool kES>
 __device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c, int k, int v) {
   const int tid = threadIdx.x, NP = K.NP, NE = K.NE;
   const int i = c % L.nx, j = c / L.nx;
@@ -428,7 +479,7 @@ __device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c,
   __syncthreads();
   if (s.iarr[I_ABW]) return false;
   // ---- R_ij(f) - r_ij, then f + dt (R - r) into VA slot 4, back to Grad form
-  cell_residual<true, true>(K, L, s, i, j,
+  cell_residual<true, true, kES>(K, L, s, i, j,
                             [&](int o, double Rr) { s.VA[4 * NP + o] = fma(s.sc[S_DT], Rr, s.cst[4 + o]); });
   __syncthreads();
   double pcell[4];
@@ -449,6 +500,7 @@ __device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c,
   return true;
 }
 
+template <bool kES>
 __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int steps, const int *queue) {
   extern __shared__ __align__(16) char smem_raw[];
   Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
@@ -478,13 +530,14 @@ __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int 
       k = (int)((item / ncell) % 4);
       c = L.order[(size_t)k * ncell + (int)(item % ncell)];
     }
-    if (!fs_item(K, L, s, c, k, 4 * st + k + 1)) break;
+    if (!fs_item<kES>(K, L, s, c, k, 4 * st + k + 1)) break;
   }
 }
 
 // FS sweeps of several problems (same M and scheme) in one persistent launch.  items[q] =
 // (problem, item of that problem's level queue); the problem descriptors (scheme constants
 // and level) are copied into shared memory per item.  All descriptors share one abort word.
+template <bool kES>
 __global__ void __launch_bounds__(kThreads) fs_batch_kernel(const BatchDesc *desc, const int2 *items,
                                                             long long total, int *counter, Consts K0) {
   extern __shared__ __align__(16) char smem_raw[];
@@ -514,13 +567,14 @@ __global__ void __launch_bounds__(kThreads) fs_batch_kernel(const BatchDesc *des
     }
     const int ncell = bd.L.ncell, qv = iv.y;
     const int st = qv / (4 * ncell), k = (qv / ncell) % 4, c = qv % ncell;
-    if (!fs_item(bd.K, bd.L, s, c, k, 4 * st + k + 1)) break;
+    if (!fs_item<kES>(bd.K, bd.L, s, c, k, 4 * st + k + 1)) break;
   }
 }
 
 // ------------------------------------------------------------------ residual of every cell
 // mode kResOut: out[c*stride + o] = R - r and the weighted norm partials;
 // kResDefect: D = -(R - r); kResCoarseRhs: rF = R + rF (the level has no r during the call).
+template <bool kES>
 __global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L, int mode, double *out,
                                                             int out_stride, double *partials) {
   extern __shared__ __align__(16) char smem_raw[];
@@ -533,7 +587,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L
     const int i = c % L.nx, j = c / L.nx;
     double loc = 0.0;
     if (mode == kResOut) {
-      cell_residual<false>(K, L, s, i, j, [&](int o, double Rr) {
+      cell_residual<false, false, kES>(K, L, s, i, j, [&](int o, double Rr) {
         if (out) out[(size_t)c * out_stride + o] = Rr;
         double w = s.fact[o] * s.sc[S_TPOW + s.tdeg[o]];
         loc += w * Rr * Rr;
@@ -544,9 +598,9 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L
       double t = block_sum(loc, s.sc + S_RED);
       if (tid == 0) acc += t * L.dx * L.dy;
     } else if (mode == kResDefect) {
-      cell_residual<false>(K, L, s, i, j, [&](int o, double Rr) { L.D[(size_t)c * NP + o] = -Rr; });
+      cell_residual<false, false, kES>(K, L, s, i, j, [&](int o, double Rr) { L.D[(size_t)c * NP + o] = -Rr; });
     } else {
-      cell_residual<false>(K, L, s, i, j,
+      cell_residual<false, false, kES>(K, L, s, i, j,
                            [&](int o, double Rr) { L.rF[(size_t)c * NP + o] = Rr + L.rF[(size_t)c * NP + o]; });
     }
     __syncthreads();
@@ -782,8 +836,10 @@ __global__ void check_state_kernel(Consts K, const double *P, const double *F, i
 static void init_attrs() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(fs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(fs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(fs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(residual_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(residual_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(restrict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(prolong_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   done = true;
@@ -796,8 +852,11 @@ static void ensure_smem_attr(Kern) {
 static size_t smem_for(const Consts &K) { return make_layout(K.M, K.N, K.NP).total; }
 
 cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, const int *queue, int grid, cudaStream_t st) {
-  ensure_smem_attr(fs_kernel);
-  fs_kernel<<<grid, kThreads, smem_for(K), st>>>(K, L, steps, queue);
+  init_attrs();
+  if (K.model == 2)
+    fs_kernel<true><<<grid, kThreads, smem_for(K), st>>>(K, L, steps, queue);
+  else
+    fs_kernel<false><<<grid, kThreads, smem_for(K), st>>>(K, L, steps, queue);
   return cudaGetLastError();
 }
 
@@ -807,21 +866,32 @@ cudaError_t launch_fs_batch(const BatchDesc *desc, const int2 *items, long long 
   if (!done) {
     // the descriptor copy is static shared memory: the dynamic part gets the rest
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, fs_batch_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, fs_batch_kernel<false>);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fs_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(fs_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024 - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncGetAttributes(&fa, fs_batch_kernel<true>);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fs_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              227 * 1024 - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return e;
     done = true;
   }
-  fs_batch_kernel<<<grid, kThreads, smem_for(K0), st>>>(desc, items, total, counter, K0);
+  if (K0.model == 2)
+    fs_batch_kernel<true><<<grid, kThreads, smem_for(K0), st>>>(desc, items, total, counter, K0);
+  else
+    fs_batch_kernel<false><<<grid, kThreads, smem_for(K0), st>>>(desc, items, total, counter, K0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const Consts &K, const LevelDev &L, int mode, double *out, int out_stride,
                             double *partials, int grid, cudaStream_t st) {
-  ensure_smem_attr(residual_kernel);
-  residual_kernel<<<grid, kThreads, smem_for(K), st>>>(K, L, mode, out, out_stride, partials);
+  init_attrs();
+  if (K.model == 2)
+    residual_kernel<true><<<grid, kThreads, smem_for(K), st>>>(K, L, mode, out, out_stride, partials);
+  else
+    residual_kernel<false><<<grid, kThreads, smem_for(K), st>>>(K, L, mode, out, out_stride, partials);
   return cudaGetLastError();
 }
 
@@ -891,14 +961,22 @@ int occupancy_cell(int M, int NP, int which) {
   size_t sm = make_layout(M, N, NP).total;
   int nb = 0;
   switch (which) {
-    case 0:
-      ensure_smem_attr(fs_kernel);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fs_kernel, kThreads, sm);
+    case 0: {  // the smaller of the two instantiations' occupancies
+      init_attrs();
+      int nb2 = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fs_kernel<false>, kThreads, sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, fs_kernel<true>, kThreads, sm);
+      nb = std::min(nb, nb2);
       break;
-    case 1:
-      ensure_smem_attr(residual_kernel);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, residual_kernel, kThreads, sm);
+    }
+    case 1: {
+      init_attrs();
+      int nb2 = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, residual_kernel<false>, kThreads, sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, residual_kernel<true>, kThreads, sm);
+      nb = std::min(nb, nb2);
       break;
+    }
     case 2:
       ensure_smem_attr(restrict_kernel);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, restrict_kernel, kThreads, sm);

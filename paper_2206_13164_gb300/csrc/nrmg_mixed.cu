@@ -402,6 +402,10 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     const float nu = ac[5], dt = ac[4];
     const float idx = (float)L.idx, idy = (float)L.idy, shk = (float)((1.0 - K.Pr) * 0.2);
     const float e2m = (ec[K.idx_2e[0]] + ec[K.idx_2e[1]] + ec[K.idx_2e[2]]) * (1.0f / 3.0f);
+    // ES-BGK: the degree-2 part of f^E is (1 - 1/Pr) times the trace-free degree-2 part of f
+    // exactly; its degree >= 4 part is quadratic in the stress and is left out of the response
+    const float esk = (float)(1.0 - 1.0 / K.Pr);
+    const int i12 = K.tab_i32[K.iq_off + 12 + 1];
     float *Eo = L.e32 + (size_t)c * NP;
     const float *Do = L.d32 + (size_t)c * NP;
     for (int q = tid; q < NE; q += kThreads) {
@@ -421,7 +425,9 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       if (o == 0 || o == K.idx_e[0] || o == K.idx_e[1])
         pe = ec[o];
       else if (o == K.idx_2e[0] || o == K.idx_2e[1] || o == K.idx_2e[2])
-        pe = e2m;
+        pe = K.model == 2 ? fmaf(esk, ec[o] - e2m, e2m) : e2m;
+      else if (K.model == 2 && o == i12)
+        pe = esk * ec[o];
       if (K.model == 1) {
         int t = s.tshak[o];
         if (t >= 0) pe = fmaf(shk, s.sc[C_Q + t], pe);

@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONPHYSICAL, ERR_NOT_CONVERGED, ERR_TIMEOUT = range(7)
-BGK, SHAKHOV = 0, 1
+BGK, SHAKHOV, ESBGK = 0, 1, 2
 
 
 class NrmgError(RuntimeError):
@@ -86,6 +86,8 @@ def lib():
         L.nrmg_set_grid.argtypes = [c_void_p, c_int]
         L.nrmg_grid_limit.restype = c_int
         L.nrmg_grid_limit.argtypes = [c_void_p]
+        L.nrmg_mixed_fallback.restype = c_int
+        L.nrmg_mixed_fallback.argtypes = [c_void_p]
         L.nrmg_set_reference.restype = c_int
         L.nrmg_set_reference.argtypes = [c_void_p, c_double, c_double]
         L.nrmg_set_state_from_fields.restype = c_int
@@ -245,6 +247,11 @@ class Solver:
         if raise_on_fail and st not in (OK, ERR_NOT_CONVERGED):
             self._check(st, "nrmg_solve")
         return st, cyc.value, rel.value
+
+    def mixed_fallback(self) -> bool:
+        """True when the last solve of a mixed-precision solver stalled and finished with FP64
+        smoothing (``nrmg_mixed_fallback``)."""
+        return bool(self.L.nrmg_mixed_fallback(self.ctx))
 
     def fields(self):
         out = torch.empty((self.ny * self.nx, 14), dtype=torch.float64, device=self.device)

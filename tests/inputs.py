@@ -16,7 +16,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-BGK, SHAKHOV = 0, 1
+BGK, SHAKHOV, ESBGK = 0, 1, 2
 
 
 def multi_indices(M: int) -> np.ndarray:

@@ -82,6 +82,10 @@ def test_create_rejects_invalid_arguments_without_a_device():
     assert L.nrmg_create(ctypes.byref(g), M, 0.1, walls, ctypes.byref(coll), ctypes.byref(o), ws, 1 << 40, None,
                          ctypes.byref(ctx)) == nrmg.ERR_ARG
     walls[2].theta = 1.0
+    # an unknown collision model (0 BGK, 1 Shakhov, 2 ES-BGK are the known ones)
+    bad_coll = nrmg.Collision(3, 2 / 3, 0.81, 1.0)
+    assert L.nrmg_create(ctypes.byref(g), M, 0.1, walls, ctypes.byref(bad_coll), ctypes.byref(o), ws, 1 << 40, None,
+                         ctypes.byref(ctx)) == nrmg.ERR_ARG
     # workspace too small
     assert L.nrmg_create(ctypes.byref(g), M, 0.1, walls, ctypes.byref(coll), ctypes.byref(o), ws, 1024, None,
                          ctypes.byref(ctx)) == nrmg.ERR_OOM
@@ -146,3 +150,4 @@ def test_net_and_learned_entry_points_check_arguments():
     L.nrmg_set_state_from_fields.restype = c_int
     L.nrmg_set_state_from_fields.argtypes = [c_void_p, c_void_p]
     assert L.nrmg_set_state_from_fields(None, None) == nrmg.ERR_ARG
+    assert L.nrmg_mixed_fallback(None) == 0

@@ -14,7 +14,7 @@ from numpy.polynomial import hermite_e as He
 import oracle
 from conftest import oracle_solver
 from hermite_quad import H_values, He_products, gauss_rule, half_line_rule, project
-from inputs import (BGK, SHAKHOV, Wall, heated_cavity, lid_cavity, maxwellian_state, multi_indices,
+from inputs import (BGK, ESBGK, SHAKHOV, Wall, heated_cavity, lid_cavity, maxwellian_state, multi_indices,
                     random_rhs, random_state)
 
 
@@ -219,6 +219,95 @@ def test_bgk_collision_vs_quadrature():
     np.testing.assert_allclose(Q, nu * (fE_coef - f), rtol=1e-10, atol=1e-12 * nu)
 
 
+def es_state(rng, M, Pr, amp=0.15):
+    """A Grad state with all six stress components set (sigma_13, sigma_23 too, so the
+    full 3x3 form of eq. ES-f^E is exercised), trace-free, with Lambda positive definite."""
+    al = multi_indices(M)
+    p = np.array([rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3), rng.uniform(-0.1, 0.1), rng.uniform(0.8, 1.3)])
+    f = rng.standard_normal(len(al)) * 0.05 * 0.5 ** np.maximum(al.sum(1) - 2, 0)
+    f[0] = rng.uniform(0.8, 1.2)
+    f[al.sum(1) == 1] = 0.0
+    S = rng.uniform(-amp, amp, (3, 3))
+    S = 0.5 * (S + S.T)
+    S -= np.trace(S) / 3 * np.eye(3)
+    sigma = S * f[0] * p[3]
+    for i in range(3):
+        for j in range(i, 3):
+            e = np.zeros(3, dtype=int)
+            e[i] += 1
+            e[j] += 1
+            f[int(np.where((al == e).all(1))[0][0])] = sigma[i, j] / (2.0 if i == j else 1.0)
+    Lam = p[3] * np.eye(3) + (1 - 1 / Pr) * sigma / f[0]
+    assert np.linalg.eigvalsh(Lam).min() > 0.2 * p[3]
+    return p, f, sigma, Lam
+
+
+@pytest.mark.parametrize("Pr", [2.0 / 3.0, 0.5])
+def test_esbgk_equilibrium_vs_quadrature(Pr):
+    """f^E of eq. (ES-f^E) projected on the cell basis.  The Gaussian of covariance Lambda is
+    integrated exactly by a tensor Gauss-Hermite rule in z, xi = u + chol(Lambda) z."""
+    M = 6
+    rng = np.random.default_rng(17)
+    al = multi_indices(M)
+    p, f, sigma, Lam = es_state(rng, M, Pr)
+    rho, u, th = f[0], p[:3], p[3]
+    x, wx = He.hermegauss(8)
+    Z = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1).reshape(-1, 3)
+    Wz = (wx[:, None, None] * wx[None, :, None] * wx[None, None, :]).reshape(-1) / (2 * math.pi) ** 1.5
+    xi = u[None, :] + Z @ np.linalg.cholesky(Lam).T
+    P = He_products(al, u, th, xi)
+    fact = np.array([math.factorial(a) * math.factorial(b) * math.factorial(c) for a, b, c in al], dtype=float)
+    fE_coef = rho * (Wz[:, None] * P).sum(0) * th ** (al.sum(1) / 2.0) / fact
+    Kn, omega, beta = 0.3, 0.81, Pr
+    nu = beta * math.sqrt(math.pi / 2) * rho * th ** (1 - omega) / Kn
+    Q = oracle.collision(M, ESBGK, Kn, Pr, omega, beta, p, f)
+    np.testing.assert_allclose(Q, nu * (fE_coef - f), rtol=1e-10, atol=1e-12 * nu)
+
+
+def test_esbgk_conservation_and_relaxation_rates():
+    """Mass, momentum and energy are conserved; the stress relaxes at nu/Pr (the property
+    that gives ES-BGK its Prandtl number) and the heat flux and other odd moments at nu."""
+    M = 7
+    Pr = 2.0 / 3.0
+    rng = np.random.default_rng(18)
+    al = multi_indices(M)
+    deg = al.sum(1)
+    p, f, sigma, Lam = es_state(rng, M, Pr)
+    nu = Pr * math.sqrt(math.pi / 2) * f[0] * p[3] ** (1 - 0.81) / 0.2
+    Q = oracle.collision(M, ESBGK, 0.2, Pr, 0.81, Pr, p, f)
+    assert abs(Q[0]) <= 1e-14 * nu and np.abs(Q[deg == 1]).max() <= 1e-14 * nu
+    two = [int(np.where((al == e).all(1))[0][0]) for e in ([2, 0, 0], [0, 2, 0], [0, 0, 2])]
+    assert abs(Q[two].sum()) <= 1e-13 * nu
+    np.testing.assert_allclose(Q[deg == 2], -(nu / Pr) * f[deg == 2], rtol=1e-13, atol=1e-16)
+    odd = deg % 2 == 1
+    np.testing.assert_allclose(Q[odd], -nu * f[odd], rtol=1e-13, atol=1e-16)
+    # degree 4: the Gaussian's fourth cumulant vanishes, so f^E_alpha = rho [s^alpha] (s^T B s)^2 / 8
+    B = (Lam - p[3] * np.eye(3))
+    for o in np.where(deg == 4)[0]:
+        a = al[o]
+        c = 0.0  # coefficient of s^a in (s^T B s)^2 / 8 = (sum_ij B_ij s_i s_j)^2 / 8
+        for i, j, k, l in np.ndindex(3, 3, 3, 3):
+            e = np.zeros(3, dtype=int)
+            for d in (i, j, k, l):
+                e[d] += 1
+            if (e == a).all():
+                c += B[i, j] * B[k, l] / 8.0
+        assert abs(Q[o] - nu * (f[0] * c - f[o])) <= 1e-12 * nu
+
+
+def test_esbgk_pr1_equals_bgk():
+    M = 5
+    rng = np.random.default_rng(33)
+    P, F = random_state(rng, 8, 8, M)
+    out = []
+    for model, Pr in ((BGK, 2 / 3), (ESBGK, 1.0)):
+        S = oracle_solver(lid_cavity(8, M, 0.2, 0.2, order=2, slope=2, model=model, Pr=Pr))
+        S.set_state(0, P, F)
+        S.smooth(0, 1)
+        out.append(S.get_state(0))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 # ------------------------------------------------------------------ interior flux
 def test_hll_consistency_equal_states():
     """Identical states on both sides: the flux is the exact projected flux P_M xi_n f."""
@@ -338,7 +427,7 @@ def test_wall_flux_of_wall_maxwellian_is_exact_flux():
 
 # ------------------------------------------------------------------ (v) Maxwellian fixed point
 @pytest.mark.parametrize("order,slope", [(1, 0), (2, 1), (2, 2)])
-@pytest.mark.parametrize("model", [BGK, SHAKHOV])
+@pytest.mark.parametrize("model", [BGK, SHAKHOV, ESBGK])
 @pytest.mark.parametrize("M", [3, 5])
 def test_maxwellian_is_fixed_point(order, slope, model, M):
     prob = lid_cavity(8, M, 0.1, 0.0, order=order, slope=slope, levels=2, model=model)
