@@ -154,6 +154,20 @@ nrmg_status nrmg_set_rhs(nrmg_ctx *ctx, int level, const double *dev_rparams, co
  * wavefronts with per-cell dependency counters).  Asynchronous. */
 nrmg_status nrmg_smooth(nrmg_ctx *ctx, int level, int steps);
 
+/* `steps` forward Euler steps on level `level` (Sec. 2.4, eq. euler-scheme),
+ * the paper's comparison scheme (not part of the multigrid cycle): every cell
+ * advances from the same old state with one step for the whole level, the
+ * smallest local step of eq. (local-CFL) (eq. global-CFL; each capped at
+ * dtnu / nu when dtnu > 0), then returns to Grad form.  Uses the level's
+ * defect buffer.  Asynchronous. */
+nrmg_status nrmg_euler(nrmg_ctx *ctx, int level, int steps);
+
+/* Forward Euler steps on the finest level until ||R(f)|| / ||R(f^0)|| <= tol
+ * (eq. relative-residual) or max_steps; *steps_out (may be NULL) = the steps
+ * taken, *rel_res_out (may be NULL) = the final relative residual.
+ * NRMG_ERR_NOT_CONVERGED when tol was not reached.  Synchronizes every step. */
+nrmg_status nrmg_euler_solve(nrmg_ctx *ctx, double tol, int max_steps, int *steps_out, double *rel_res_out);
+
 /* R_ij(f) - r_ij of every cell of level `level` (eq. ode-system, each row in
  * its cell's basis) into dev_R_out ([cells][N_M], may be NULL), and the
  * residual norm of eq. (relative-residual) into *norm_out (may be NULL;

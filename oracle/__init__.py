@@ -91,6 +91,8 @@ def lib():
         L.or_sweep.argtypes = [c_void_p, c_int, c_int]
         L.or_smooth.restype = c_int
         L.or_smooth.argtypes = [c_void_p, c_int, c_int]
+        L.or_euler.restype = c_int
+        L.or_euler.argtypes = [c_void_p, c_int, c_int]
         L.or_cell_residual.argtypes = [c_void_p, c_int, c_int, c_int, _dp]
         L.or_residual.restype = c_double
         L.or_residual.argtypes = [c_void_p, c_int, _dp]
@@ -245,6 +247,10 @@ class Solver:
 
     def smooth(self, level, steps):
         return self.L.or_smooth(self.h, level, steps)
+
+    def euler(self, level, steps):
+        """steps forward Euler steps (eq. euler-scheme, global step of eq. global-CFL)."""
+        return self.L.or_euler(self.h, level, steps)
 
     def cell_residual(self, level, i, j):
         R = np.zeros(self.n)

@@ -20,6 +20,7 @@
  *                                                  eq. (BGK-f^E), eq. (Shakhov-f^E), eq. (ES-f^E);
  *                                                  Sec. 4, eq. (nu-shakhov)
  *   - local time step, two-step update ............ Sec. 2.4, eq. (local-CFL)
+ *   - forward Euler step .......................... Sec. 2.4, eq. (euler-scheme), eq. (global-CFL)
  *   - fast sweeping step FS(f, r) ................. Sec. 3.1, Algorithm 1
  *   - restriction / prolongation .................. Sec. 3.2.2, eq. (uH-thetaH-computation),
  *                                                  eq. (fH), eq. (rewritten-update)
@@ -744,16 +745,22 @@ static int regrad(const or_solver *S, const double *p, const double *g, double *
 /*   the cap changes the iteration, not its fixed point);               */
 /*   f <- f + dt (R_ij(f) - r_ij), then back to Grad form.             */
 /* ------------------------------------------------------------------ */
-static int cell_update(or_solver *S, or_level *L, int i, int j) {
-  int n = S->n, c = j * L->nx + i;
-  double *pc = L->P + 4 * c, *fc = L->F + (size_t)c * n;
-  double R[OR_MAXN], r[OR_MAXN], g[OR_MAXN], pn[4], fn[OR_MAXN];
+static double local_dt(const or_solver *S, const or_level *L, int c) {
+  const double *pc = L->P + 4 * c, *fc = L->F + (size_t)c * S->n;
   double sq = sqrt(pc[3]);
   double dt = S->c.cfl / ((fabs(pc[0]) + S->C * sq) / L->dx + (fabs(pc[1]) + S->C * sq) / L->dy);
   if (S->c.dtnu > 0.0) {
     double nu = S->c.beta * sqrt(M_PI / 2.0) * fc[0] * pow(pc[3], 1.0 - S->c.omega) / S->c.Kn;
     dt = fmin(dt, S->c.dtnu / nu);
   }
+  return dt;
+}
+
+static int cell_update(or_solver *S, or_level *L, int i, int j) {
+  int n = S->n, c = j * L->nx + i;
+  double *pc = L->P + 4 * c, *fc = L->F + (size_t)c * n;
+  double R[OR_MAXN], r[OR_MAXN], g[OR_MAXN], pn[4], fn[OR_MAXN];
+  double dt = local_dt(S, L, c);
   cell_R(S, L, i, j, R);
   rhs_in(S, L, c, pc, r);
   for (int o = 0; o < n; ++o) g[o] = fc[o] + dt * (R[o] - r[o]);
@@ -788,6 +795,38 @@ int or_smooth(or_solver *S, int l, int steps) {
       int e = or_sweep(S, l, k);
       if (e != OR_OK) st = e;
     }
+  return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* Forward Euler (Sec. 2.4, eq. euler-scheme): every cell advances     */
+/* from the same old state f^n, with one step for the whole level: the */
+/* smallest local step of eq. (local-CFL) (eq. global-CFL; with the    */
+/* dtnu cap when it is set); then each cell returns to Grad form.      */
+/* ------------------------------------------------------------------ */
+int or_euler(or_solver *S, int l, int steps) {
+  or_level *L = &S->lev[l];
+  int n = S->n, nc = L->nx * L->ny, st = OR_OK;
+  double *G = (double *)malloc(sizeof(double) * (size_t)nc * n);
+  double R[OR_MAXN], r[OR_MAXN], pn[4], fn[OR_MAXN];
+  for (int s = 0; s < steps; ++s) {
+    double dt = INFINITY;
+    for (int c = 0; c < nc; ++c) dt = fmin(dt, local_dt(S, L, c));
+    for (int j = 0; j < L->ny; ++j)
+      for (int i = 0; i < L->nx; ++i) {
+        int c = j * L->nx + i;
+        cell_R(S, L, i, j, R);
+        rhs_in(S, L, c, L->P + 4 * c, r);
+        for (int o = 0; o < n; ++o) G[(size_t)c * n + o] = L->F[(size_t)c * n + o] + dt * (R[o] - r[o]);
+      }
+    for (int c = 0; c < nc; ++c) {
+      int e = regrad(S, L->P + 4 * c, G + (size_t)c * n, pn, fn);
+      if (e != OR_OK) st = e;
+      memcpy(L->P + 4 * c, pn, 4 * sizeof(double));
+      memcpy(L->F + (size_t)c * n, fn, n * sizeof(double));
+    }
+  }
+  free(G);
   return st;
 }
 

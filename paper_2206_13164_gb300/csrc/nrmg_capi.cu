@@ -905,6 +905,67 @@ nrmg_status nrmg_smooth(nrmg_ctx *ctx, int level, int steps) {
   return smooth(ctx, level, steps);
 }
 
+// One forward Euler step of `level` (eq. euler-scheme): R - r of the old state into the level's
+// defect buffer, with the norm partials; when norm_host is given, its norm (synchronizes) and,
+// if that is at or below stop_at, no update; else the global step and the update.
+static nrmg_status euler_step(nrmg_ctx *ctx, int level, double stop_at, double *norm_host, bool *stopped) {
+  LevelDev &L = ctx->lev[level];
+  int g = 0;
+  nrmg_status s = residual(ctx, level, kResOut, L.D, ctx->NP, &g);
+  if (s != NRMG_OK) return s;
+  if (stopped) *stopped = false;
+  if (norm_host) {
+    CK(launch_reduce_norm(ctx->partials, g, 1.0 / (ctx->grid.lx * ctx->grid.ly), ctx->dscal, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hpin, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((s = sync_status(ctx)) != NRMG_OK) return s;
+    *norm_host = ctx->hpin[0];
+    ctx->launches += 1;
+    if (*norm_host <= stop_at) {
+      if (stopped) *stopped = true;
+      return NRMG_OK;
+    }
+  }
+  CK(launch_euler(ctx->K, L, ctx->dscal + 8, grid_for(ctx, 3, L.ncell), ctx->stream));
+  ctx->launches += 2;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_euler(nrmg_ctx *ctx, int level, int steps) {
+  if (!ctx || level < 0 || level >= ctx->levels || steps < 0) return NRMG_ERR_ARG;
+  for (int n = 0; n < steps; ++n) {
+    nrmg_status s = euler_step(ctx, level, 0.0, nullptr, nullptr);
+    if (s != NRMG_OK) return s;
+  }
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_euler_solve(nrmg_ctx *ctx, double tol, int max_steps, int *steps_out, double *rel_res_out) {
+  if (!ctx || !(tol >= 0.0) || max_steps < 0) return NRMG_ERR_ARG;
+  const int K = ctx->levels - 1;
+  ctx->lev[K].has_r = 0;
+  nrmg_status s;
+  if (!ctx->ref_fixed) {
+    if ((s = norm_of(ctx, K, nullptr, &ctx->res0)) != NRMG_OK) return s;
+    ctx->have_res0 = 1;
+  }
+  const double ref = ctx->res0;
+  double nrm = 0.0, rr = ref > 0.0 ? 1.0 : 0.0;
+  int n = 0;
+  for (;;) {
+    bool stopped = false;
+    const bool last = n >= max_steps;
+    // at the step budget only the norm is wanted: stop_at = infinity skips the update
+    if ((s = euler_step(ctx, K, last ? INFINITY : tol * ref, &nrm, &stopped)) != NRMG_OK) break;
+    rr = ref > 0.0 ? nrm / ref : 0.0;
+    if (stopped) break;
+    ++n;
+  }
+  if (steps_out) *steps_out = n;
+  if (rel_res_out) *rel_res_out = rr;
+  if (s == NRMG_OK && rr > tol) s = NRMG_ERR_NOT_CONVERGED;
+  return s;
+}
+
 nrmg_status nrmg_residual(nrmg_ctx *ctx, int level, double *dev_R_out, double *norm_out) {
   if (!ctx || level < 0 || level >= ctx->levels) return NRMG_ERR_ARG;
   if (norm_out) return norm_of(ctx, level, dev_R_out, norm_out);

@@ -91,6 +91,9 @@ cudaError_t launch_residual(const Consts &K, const LevelDev &L, int mode, double
                             double *partials, int grid, cudaStream_t st);
 cudaError_t launch_restrict(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st);
 cudaError_t launch_prolong(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st);
+// one forward Euler step (eq. euler-scheme) of a level whose L.D holds R - r of the state;
+// dt_dev receives the global step
+cudaError_t launch_euler(const Consts &K, const LevelDev &L, double *dt_dev, int grid, cudaStream_t st);
 cudaError_t launch_reduce_norm(const double *partials, int n, double scale, double *out, cudaStream_t st);
 // Total mass of level L into scal[0]; with apply, also scale every coefficient by m0 / mass
 // (scal[1]).

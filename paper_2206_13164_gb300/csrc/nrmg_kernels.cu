@@ -742,6 +742,58 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(Consts K, LevelDev Lf
   }
 }
 
+// ------------------------------------------------------------------ forward Euler (Sec. 2.4)
+// The level's step of eq. (global-CFL): the smallest local step of eq. (local-CFL) over the
+// level (each capped at dtnu / nu when dtnu > 0), reduced by one block.
+__global__ void euler_dt_kernel(Consts K, LevelDev L, double *dt_out) {
+  __shared__ double red[kThreads];
+  double m = INFINITY;
+  for (int c = threadIdx.x; c < L.ncell; c += kThreads) {
+    const double *p = L.P + (size_t)c * 4;
+    const double sq = sqrt(p[3]);
+    double dt = K.cfl / ((fabs(p[0]) + K.C * sq) * L.idx + (fabs(p[1]) + K.C * sq) * L.idy);
+    if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / (K.nu0 * L.F[(size_t)c * K.NP] * L.tp[c]));
+    m = fmin(m, dt);
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dt_out[0] = red[0];
+}
+
+// eq. (euler-scheme): f <- Grad(f + dt (R(f) - r)) for every cell, with R - r of the old state
+// in L.D (written by the residual kernel before any cell changes) and dt from euler_dt_kernel.
+__global__ void __launch_bounds__(kThreads) euler_update_kernel(Consts K, LevelDev L, const double *dt_in) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
+  load_tables(K, s);
+  __syncthreads();
+  const int tid = threadIdx.x, NE = K.NE, NP = K.NP;
+  const double dt = *dt_in;
+  for (int c = blockIdx.x; c < L.ncell; c += gridDim.x) {
+    for (int q = tid; q < NE; q += kThreads) {
+      const int o = s.eidx[q];
+      s.VA[o] = fma(dt, L.D[(size_t)c * NP + o], L.F[(size_t)c * NP + o]);
+    }
+    if (tid < 4) s.sc[S_PH + tid] = L.P[(size_t)c * 4 + tid];
+    __syncthreads();
+    double pcell[4];
+    for (int e = 0; e < 4; ++e) pcell[e] = s.sc[S_PH + e];
+    bool ok = regrad(K, s, pcell, 0, true);
+    for (int q = tid; q < NE; q += kThreads) {
+      const int o = s.eidx[q];
+      L.F[(size_t)c * NP + o] = s.VB[o];
+    }
+    if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+    if (tid == 4) L.tp[c] = s.sc[S_TPN];
+    if (!ok && tid == 0) raise_status(K, kStNonPhysical, false);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ reductions and small kernels
 __global__ void reduce_norm_kernel(const double *partials, int n, double scale, double *out) {
   __shared__ double red[kThreads / 32];
@@ -842,6 +894,7 @@ static void init_attrs() {
   cudaFuncSetAttribute(residual_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(restrict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(prolong_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(euler_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   done = true;
 }
 template <typename Kern>
@@ -904,6 +957,13 @@ cudaError_t launch_restrict(const Consts &K, const LevelDev &Lf, const LevelDev 
 cudaError_t launch_prolong(const Consts &K, const LevelDev &Lf, const LevelDev &Lc, int grid, cudaStream_t st) {
   ensure_smem_attr(prolong_kernel);
   prolong_kernel<<<grid, kThreads, smem_for(K), st>>>(K, Lf, Lc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_euler(const Consts &K, const LevelDev &L, double *dt_dev, int grid, cudaStream_t st) {
+  init_attrs();
+  euler_dt_kernel<<<1, kThreads, 0, st>>>(K, L, dt_dev);
+  euler_update_kernel<<<grid, kThreads, smem_for(K), st>>>(K, L, dt_dev);
   return cudaGetLastError();
 }
 

@@ -88,6 +88,10 @@ def lib():
         L.nrmg_grid_limit.argtypes = [c_void_p]
         L.nrmg_mixed_fallback.restype = c_int
         L.nrmg_mixed_fallback.argtypes = [c_void_p]
+        L.nrmg_euler.restype = c_int
+        L.nrmg_euler.argtypes = [c_void_p, c_int, c_int]
+        L.nrmg_euler_solve.restype = c_int
+        L.nrmg_euler_solve.argtypes = [c_void_p, c_double, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]
         L.nrmg_set_reference.restype = c_int
         L.nrmg_set_reference.argtypes = [c_void_p, c_double, c_double]
         L.nrmg_set_state_from_fields.restype = c_int
@@ -247,6 +251,19 @@ class Solver:
         if raise_on_fail and st not in (OK, ERR_NOT_CONVERGED):
             self._check(st, "nrmg_solve")
         return st, cyc.value, rel.value
+
+    def euler(self, steps, level=None):
+        """``steps`` forward Euler steps (eq. euler-scheme) on a level (default: the finest)."""
+        level = self.levels - 1 if level is None else level
+        self._check(self.L.nrmg_euler(self.ctx, level, steps), "nrmg_euler")
+
+    def euler_solve(self, tol=1e-8, max_steps=100000, raise_on_fail=True):
+        """Forward Euler on the finest level to relative residual tol: (status, steps, rel)."""
+        n, rel = c_int(0), c_double(0.0)
+        st = self.L.nrmg_euler_solve(self.ctx, tol, max_steps, ctypes.byref(n), ctypes.byref(rel))
+        if raise_on_fail and st not in (OK, ERR_NOT_CONVERGED):
+            self._check(st, "nrmg_euler_solve")
+        return st, n.value, rel.value
 
     def mixed_fallback(self) -> bool:
         """True when the last solve of a mixed-precision solver stalled and finished with FP64

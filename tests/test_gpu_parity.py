@@ -94,6 +94,22 @@ def test_fs_step_parity(name, prob, amp):
     assert_close(N(Fg), Fo, 1e-12, "coeffs")
 
 
+@pytest.mark.parametrize("name", ["lid_dtnu_M4_12", "heat_shak_o2va_M5_16", "lid_esbgk_o2va_M8_12x9"])
+def test_euler_step_parity(name):
+    """Forward Euler (eq. euler-scheme, global step of eq. global-CFL), three steps."""
+    prob, amp = {c[0]: (c[1], c[2]) for c in CASES}[name]
+    rng = np.random.default_rng(104)
+    P, F = random_state(rng, prob.ny, prob.nx, prob.M, amp=amp)
+    G, O = gpu(prob), oracle_solver(prob)
+    set_both(G, O, 0, P, F)
+    G.euler(3, 0)
+    assert O.euler(0, 3) == 0
+    Pg, Fg = G.get_state(0)
+    Po, Fo = O.get_state(0)
+    assert_close(N(Pg), Po, 1e-12, "params")
+    assert_close(N(Fg), Fo, 1e-12, "coeffs")
+
+
 def test_fs_parity_with_rhs_and_several_steps():
     prob = lid_cavity(12, 5, 0.1, 0.3, order=2, slope=2)
     rng = np.random.default_rng(102)
@@ -499,9 +515,12 @@ def _check_paper_rows(rows):
         else:
             prob = heated_cavity(N, M, kn, theta_bottom=2.0, order=order, slope=slope, levels=levels_to_8(N),
                                  model=SHAKHOV)
-        if solver == "FS":
+        if solver in ("FS", "Euler"):
             prob = prob.replace(levels=1, s3=1)
-        st, cyc, rel = nrmg.from_problem(prob, device=DEV).solve(1e-8, 4000 if solver == "FS" else 100)
+        if solver == "Euler":
+            st, cyc, rel = nrmg.from_problem(prob, device=DEV).euler_solve(1e-8, 40000)
+        else:
+            st, cyc, rel = nrmg.from_problem(prob, device=DEV).solve(1e-8, 4000 if solver == "FS" else 100)
         assert st == 0 and rel <= 1e-8, (src, case, N, M, solver)
         if tol.endswith("%"):
             assert abs(cyc - printed) <= printed * float(tol[:-1]) / 100, (src, case, N, M, solver, cyc, printed)
@@ -514,8 +533,8 @@ def _check_paper_rows(rows):
 def test_iteration_counts_against_the_papers_tables():
     """The paper's printed iteration counts (Tables 1, 2, 3, 6, 8, 9: Shakhov lid-driven,
     four-sided and bottom-heated cavities, first and second order, M up to 15): the GPU's FAS
-    cycle needs within two cycles of each asserted count, single-level FS within 30% of the
-    printed steps
+    cycle needs within two cycles of each asserted count, single-level FS and forward Euler
+    within 30% of the printed steps
     (the flux and wall readings are this repository's), and on 32x32 the oracle's cycle
     count."""
     import math
@@ -532,6 +551,6 @@ def test_iteration_counts_against_the_papers_tables():
 def test_esbgk_iteration_counts_against_table4():
     """Table 4 of the paper (ES-BGK, beta = Pr = 2/3, single lid-driven cavity on 64x64, first
     order): the FAS cycle within two cycles of the printed counts for M = 5, 10, 15 at
-    Kn = 0.1 and M = 5, 10 at Kn = 1, single-level FS within 30% for M = 5."""
+    Kn = 0.1 and M = 5, 10 at Kn = 1, single-level FS and forward Euler within 30% for M = 5."""
     seen = _check_paper_rows([r for r in _paper_rows() if r[0] == "Table4"])
-    assert len(seen) >= 7
+    assert len(seen) >= 9

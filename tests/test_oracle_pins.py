@@ -308,6 +308,69 @@ def test_esbgk_pr1_equals_bgk():
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
+# ------------------------------------------------------------------ forward Euler (comparison scheme)
+def test_euler_step_is_jacobi_with_the_global_cfl_step():
+    """eq. (euler-scheme) with eq. (global-CFL): every cell moves from the same old state by
+    the smallest local step of eq. (local-CFL); rebuilt here from the residual of the old state,
+    the largest He_{M+1} root from numpy, and the (separately pinned) macroscopics and basis
+    transform."""
+    M = 4
+    prob = lid_cavity(8, M, 0.2, 0.3, order=2, slope=2).replace(ny=6)
+    rng = np.random.default_rng(41)
+    P, F = random_state(rng, prob.ny, prob.nx, M)
+    O = oracle_solver(prob)
+    O.set_state(0, P, F)
+    R, _ = O.residual(0)
+    C = He.hermeroots([0] * (M + 1) + [1]).real.max()
+    dx, dy = 1.0 / prob.nx, 1.0 / prob.ny
+    sq = np.sqrt(P[:, 3])
+    dt = (prob.cfl / ((np.abs(P[:, 0]) + C * sq) / dx + (np.abs(P[:, 1]) + C * sq) / dy)).min()
+    al = multi_indices(M)
+    e1 = [int(np.where((al == e).all(1))[0][0]) for e in ([1, 0, 0], [0, 1, 0], [0, 0, 1])]
+    e2 = [int(np.where((al == e).all(1))[0][0]) for e in ([2, 0, 0], [0, 2, 0], [0, 0, 2])]
+    P1, F1 = np.zeros_like(P), np.zeros_like(F)
+    for c in range(P.shape[0]):
+        g = F[c] + dt * R[c]
+        mac = oracle.macros(M, P[c], g)
+        P1[c] = mac[1:]
+        F1[c] = oracle.transform(M, P[c], P1[c], g)
+        F1[c, e1] = 0.0
+        F1[c, e2] -= F1[c, e2].mean()
+    assert O.euler(0, 1) == 0
+    Po, Fo = O.get_state(0)
+    np.testing.assert_allclose(Po, P1, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(Fo, F1, rtol=0, atol=1e-13 * np.abs(F1).max())
+    # mass: the fluxes cancel pairwise and the walls carry none
+    assert abs(Fo[:, 0].sum() - F[:, 0].sum()) <= 1e-13 * F[:, 0].sum()
+
+
+def test_euler_reaches_the_fs_fixed_point_more_slowly():
+    """Forward Euler conserves the total mass exactly (Jacobi update, conservative fluxes, no
+    wall mass flux), so it reaches the steady state of the initial mass, which the mass-corrected
+    FAS solve also reaches; single-level FS needs several times fewer steps (the paper's
+    Tables 1-9 show 6-9x)."""
+    prob = lid_cavity(8, 3, 0.2, 0.3, order=1)
+    S = oracle_solver(prob.replace(s3=1))
+    st, n_fs, _ = S.solve(1e-9, 5000)
+    assert st == 0
+    ref = oracle_solver(prob.replace(levels=2))
+    assert ref.solve(1e-11, 300)[0] == 0
+    E = oracle_solver(prob)
+    m0 = E.mass()
+    r0 = E.residual(0)[1]
+    n_eu = 0
+    while E.residual(0)[1] > 1e-9 * r0:
+        assert E.euler(0, 1) == 0
+        n_eu += 1
+        assert n_eu < 20000
+    assert abs(E.mass() - m0) <= 1e-13 * m0
+    fr, fe = ref.fields(), E.fields()
+    for k in range(fr.shape[-1]):
+        scale = max(np.abs(fr[..., k]).max(), 1e-3)
+        assert np.abs(fe[..., k] - fr[..., k]).max() <= 1e-6 * scale, k
+    assert n_eu >= 3 * n_fs, (n_eu, n_fs)
+
+
 # ------------------------------------------------------------------ interior flux
 def test_hll_consistency_equal_states():
     """Identical states on both sides: the flux is the exact projected flux P_M xi_n f."""
