@@ -218,9 +218,9 @@ class LearnedSolve:
 
     The first grid (`start` cells a side) is solved plainly; every finer grid up to N holds
     two contexts when a network is given: the interpolated start and the network's start.
-    Both run the same FAS cycles (`polish` below the target, `judge` on the target) and the
-    one with the smaller residual norm after them continues: the plain FAS cycle judges the
-    network.  The final solve on the target stops at tol of the plain start's residual.
+    Both run the same FAS cycles (`polish` below the target, `decide` on the target) and the
+    one with the smaller residual norm after them continues: the plain FAS cycle decides
+    whether the network's start is used.  The final solve on the target stops at tol of the plain start's residual.
     Contexts are created here, outside the timed run."""
 
     def __init__(self, N, M, Kn, U, start=64, net=None, **kw):
@@ -243,11 +243,11 @@ class LearnedSolve:
         for s in [self.coarse] + self.main + (self.twin or []):
             s.set_grid(min(ctas_per_sm, int(s.L.nrmg_grid_limit(s.ctx))))
 
-    def run(self, tol=1e-8, coarse_tol=1e-6, polish=2, judge=2, max_cycles=400, net_grids="trained",
+    def run(self, tol=1e-8, coarse_tol=1e-6, polish=2, decide=2, max_cycles=400, net_grids="trained",
             polish_tol=None):
         """net_grids: the grids on which the network's candidate is built: "trained" (default) =
         the grids no finer than the finest grid of the network's training data, None = all,
-        or a list; polish_tol: below the target, after the judged cycles, keep cycling the
+        or a list; polish_tol: below the target, after the deciding cycles, keep cycling the
         winner until its residual is polish_tol of that grid's plain start."""
         Kn, U = self.Kn, self.U
         if net_grids == "trained":
@@ -258,11 +258,11 @@ class LearnedSolve:
         st, cyc_c, _ = self.coarse.solve(coarse_tol, max_cycles)
         fields = self.coarse.fields()
         t1 = time.perf_counter()
-        log, wasted, judged = [], 0, 0
+        log, wasted, decided = [], 0, 0
         target = None
         for k, n in enumerate(self.grids):
             last = k + 1 == len(self.grids)
-            cyc = judge if last else polish
+            cyc = decide if last else polish
             pro, x = features(fields, Kn, U)
             cands = [self.main[k]]
             self.main[k].set_state_from_fields(pro)
@@ -290,7 +290,7 @@ class LearnedSolve:
             log.append(rec)
             if last:
                 target = cands[w]
-                judged = cyc
+                decided = cyc
             else:
                 if polish_tol is not None:
                     cands[w].set_reference(res0=self.res0_grid[k])
@@ -305,10 +305,10 @@ class LearnedSolve:
         torch.cuda.synchronize()
         t3 = time.perf_counter()
         self.target = target
-        return {"status": st, "cycles": judged + cyc, "final_cycles": cyc, "wasted_cycles": wasted,
+        return {"status": st, "cycles": decided + cyc, "final_cycles": cyc, "wasted_cycles": wasted,
                 "rel_res": rel, "rel_res_after_climb": rel_start, "coarse_cycles": cyc_c, "t_coarse": t1 - t0,
                 "t_climb": t2 - t1, "t_final": t3 - t2, "t_total": t3 - t0, "climb": log, "polish": polish,
-                "judge": judge}
+                "decide": decide}
 
 
 def plain_solve(N, M, Kn, U, tol=1e-8, max_cycles=400, grid=0, **kw):
@@ -407,7 +407,7 @@ def train(net, data, epochs, batch=16, lr=2e-3, lr_min=2e-5, wd=1e-4, seed=0, lo
     return hist
 
 
-def evaluate(N, M, Kn, U, net, start=64, polish=2, judge=2, tol=1e-8, grid=0, mixed=False):
+def evaluate(N, M, Kn, U, net, start=64, polish=2, decide=2, tol=1e-8, grid=0, mixed=False):
     """Cycles and wall time to tol on one cavity: plain start, climb without the network, climb
     with it (and, with mixed, the plain start and the climb with the network on the
     mixed-precision smoother); the largest field difference of each against the plain
@@ -424,7 +424,7 @@ def evaluate(N, M, Kn, U, net, start=64, polish=2, judge=2, tol=1e-8, grid=0, mi
     for name, nn, prec in runs:
         ls = LearnedSolve(N, M, Kn, U, start=start, net=nn, precision=prec)
         ls.set_grid(grid)
-        r = ls.run(tol=tol, polish=polish, judge=judge)
+        r = ls.run(tol=tol, polish=polish, decide=decide)
         r["max_field_diff"] = float((ls.target.fields() - ref).abs().max())
         out[name] = r
         del ls
@@ -452,7 +452,7 @@ def main(argv=None):
     ev.add_argument("--U", type=float, default=0.35)
     ev.add_argument("--start", type=int, default=64)
     ev.add_argument("--polish", type=int, default=2)
-    ev.add_argument("--judge", type=int, default=2)
+    ev.add_argument("--decide", type=int, default=2)
     ev.add_argument("--weights", default=WEIGHTS)
     pr = sub.add_parser("profile", help="a few forward passes and training steps on one image (profiling case)")
     pr.add_argument("--N", type=int, default=512)
@@ -470,7 +470,7 @@ def main(argv=None):
         return
     if a.cmd == "eval":
         print(json.dumps(evaluate(a.N, a.M, a.Kn, a.U, Net.load(a.weights, max_pixels=a.N * a.N), start=a.start,
-                                  polish=a.polish, judge=a.judge)), flush=True)
+                                  polish=a.polish, decide=a.decide)), flush=True)
         return
     rng = np.random.default_rng(a.seed)
     t_start = time.perf_counter()

@@ -173,7 +173,7 @@ def test_grad_state_reproduces_fields(L):
 
 @pytest.mark.parametrize("with_net", [False, True])
 def test_learned_solve_reaches_the_plain_solution(L, with_net):
-    """A network (here random, untrained) cannot change the answer: the candidates are judged by
+    """A network (here random, untrained) cannot change the answer: the candidates are chosen by
     the residual after the same FAS cycles and the final cycles stop at 1e-8 of the plain
     start's residual, so the fields equal those of the plain solve."""
     Kn, U, M = 0.1, 0.3, 5
@@ -181,7 +181,7 @@ def test_learned_solve_reaches_the_plain_solution(L, with_net):
     plain, rec = L.plain_solve(32, M, Kn, U)
     assert rec["status"] == 0
     ls = L.LearnedSolve(32, M, Kn, U, start=16, net=net)
-    out = ls.run(tol=1e-8, coarse_tol=1e-6, polish=2, judge=2)
+    out = ls.run(tol=1e-8, coarse_tol=1e-6, polish=2, decide=2)
     assert out["status"] == 0 and out["rel_res"] <= 1e-8
     assert out["cycles"] < rec["cycles"]
     assert out["wasted_cycles"] == (2 if with_net else 0)
