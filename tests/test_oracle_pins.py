@@ -501,10 +501,11 @@ def test_maxwellian_is_fixed_point(order, slope, model, M):
 
 
 # ------------------------------------------------------------------ (vi) conservation
+@pytest.mark.parametrize("model", [BGK, SHAKHOV, ESBGK])
 @pytest.mark.parametrize("order,slope", [(1, 0), (2, 2)])
-def test_residual_conserves_mass(order, slope):
+def test_residual_conserves_mass(order, slope, model):
     M = 4
-    prob = lid_cavity(8, M, 0.1, 0.3, order=order, slope=slope)
+    prob = lid_cavity(8, M, 0.1, 0.3, order=order, slope=slope, model=model)
     S = oracle_solver(prob)
     rng = np.random.default_rng(30)
     P, F = random_state(rng, 8, 8, M)
@@ -550,11 +551,12 @@ def test_shakhov_pr1_equals_bgk():
 
 
 # ------------------------------------------------------------------ (viii) mirror symmetry
+@pytest.mark.parametrize("model", [SHAKHOV, ESBGK])
 @pytest.mark.parametrize("order,slope", [(1, 0), (2, 2)])
-def test_residual_reflection_equivariance(order, slope):
+def test_residual_reflection_equivariance(order, slope, model):
     M = 5
     N = 8
-    prob = heated_cavity(N, M, 0.3, order=order, slope=slope)
+    prob = heated_cavity(N, M, 0.3, order=order, slope=slope, model=model)
     S = oracle_solver(prob)
     rng = np.random.default_rng(33)
     P, F = random_state(rng, N, N, M)
@@ -576,9 +578,10 @@ def test_residual_reflection_equivariance(order, slope):
 
 
 # ------------------------------------------------------------------ (ix) xi_3 parity
-def test_odd_alpha3_stays_zero():
+@pytest.mark.parametrize("model", [BGK, ESBGK])
+def test_odd_alpha3_stays_zero(model):
     M = 5
-    prob = lid_cavity(8, M, 0.1, 0.4, order=2, slope=2, levels=2)
+    prob = lid_cavity(8, M, 0.1, 0.4, order=2, slope=2, levels=2, model=model)
     S = oracle_solver(prob)
     rng = np.random.default_rng(34)
     S.set_state(1, *random_state(rng, 8, 8, M))
