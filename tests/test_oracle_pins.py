@@ -666,6 +666,22 @@ def test_fas_converges_and_conserves_mass():
     assert f[-1, :, 1].mean() > 0 > f[0, :, 1].mean()
 
 
+def test_esbgk_fas_converges_with_the_gas_dragged_by_the_lid():
+    """ES-BGK (beta = Pr = 2/3) through the whole FAS cycle: converges, keeps the mass, and the
+    stress sigma_12 under the lid has the sign of a viscous stress, -mu du_1/dy < 0 (the gas
+    above moves faster)."""
+    prob = lid_cavity(16, 4, 0.1, 0.3, levels=2, order=2, slope=2, model=ESBGK, beta=2 / 3)
+    S = oracle_solver(prob)
+    m0 = S.mass()
+    st, cyc, rel = S.solve(1e-8, 80)
+    assert st == oracle.OK and rel <= 1e-8 and cyc < 40
+    assert abs(S.mass() - m0) < 1e-13
+    f = S.fields()  # rho, u (3), theta, sigma_11, sigma_12, ..., q (3)
+    assert np.all(f[..., 0] > 0) and np.all(f[..., 4] > 0)
+    assert f[-1, :, 1].mean() > 0 > f[0, :, 1].mean()
+    assert f[-1, :, 6].mean() < 0
+
+
 def test_multigrid_cycle_count_is_flat_fs_doubles():
     """Sec. 3.1/3.2 behaviour: FS iterations grow with the grid, NMG cycles stay nearly flat."""
     cyc = {}
