@@ -5,9 +5,14 @@ CPU-baseline leg of ``bench.py`` may import this package.  The oracle is plain s
 (``nrmg_oracle.c``) compiled with gcc; this module builds it and wraps it with ctypes.
 It shares no code with the CUDA library.
 
-Functions whose parity with the paper is UNPINNED (the paper prints no formula):
-the interior numerical flux (HLL reading), the Maxwell wall flux (half-range reading),
-the limited slope (van Albada reading) and the mass correction after each NMG step.
+Readings whose parity with the paper is UNPINNED (the paper prints no formula): the
+interior numerical flux (HLL reading), the Maxwell wall flux (half-range reading) and the mass
+correction after each NMG step.  Each reading is itself pinned (tests/test_oracle_pins*.py):
+the HLL flux by its consistency, upwind limits, conservation, intermediate-state form and
+Rusanov special case; the wall flux by velocity-space quadrature; the van Albada slope (the
+limiter reading; the paper prints the central slope) by its defining properties; the FAS
+defect, restriction, coarse right-hand side and coarse-grid update by exact identities of the
+cycle.  tests/test_oracle_mutants.py checks that planted mistakes in these parts fail them.
 """
 from __future__ import annotations
 
@@ -56,58 +61,65 @@ _dp = POINTER(c_double)
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
-        L.or_create.restype = c_void_p
-        L.or_create.argtypes = [POINTER(OrConfig)]
-        L.or_destroy.argtypes = [c_void_p]
-        for name in ("or_level_nx", "or_level_ny"):
-            getattr(L, name).restype = c_int
-            getattr(L, name).argtypes = [c_void_p, c_int]
-        L.or_c_m1.restype = c_double
-        L.or_c_m1.argtypes = [c_void_p]
-        L.or_nmom.restype = c_int
-        L.or_nmom.argtypes = [c_int]
-        L.or_alphas.argtypes = [c_int, POINTER(c_int)]
-        L.or_hermite_max_root.restype = c_double
-        L.or_hermite_max_root.argtypes = [c_int]
-        L.or_transform.argtypes = [c_int, _dp, _dp, _dp, _dp]
-        L.or_xi_mul.argtypes = [c_int, c_int, _dp, _dp, _dp]
-        L.or_macros.argtypes = [c_int, _dp, _dp, _dp]
-        L.or_cell_fields.argtypes = [c_int, _dp, _dp, _dp]
-        L.or_halfrange.argtypes = [c_int, c_int, _dp]
-        L.or_hll_flux.argtypes = [c_int, c_double, c_int, _dp, _dp, _dp, _dp, _dp, _dp]
-        L.or_wall_flux.argtypes = [c_int, _dp, c_double, c_double, c_int, _dp, _dp, _dp, _dp]
-        L.or_collision.argtypes = [c_int, c_int, c_double, c_double, c_double, c_double, _dp, _dp, _dp]
-        L.or_set_state.argtypes = [c_void_p, c_int, _dp, _dp]
-        L.or_get_state.argtypes = [c_void_p, c_int, _dp, _dp]
-        L.or_set_rhs.argtypes = [c_void_p, c_int, _dp, _dp]
-        L.or_get_rhs.argtypes = [c_void_p, c_int, _dp, _dp]
-        L.or_get_saved.argtypes = [c_void_p, c_int, _dp, _dp]
-        L.or_mass.restype = c_double
-        L.or_mass.argtypes = [c_void_p]
-        L.or_res0.restype = c_double
-        L.or_res0.argtypes = [c_void_p]
-        L.or_sweep.restype = c_int
-        L.or_sweep.argtypes = [c_void_p, c_int, c_int]
-        L.or_smooth.restype = c_int
-        L.or_smooth.argtypes = [c_void_p, c_int, c_int]
-        L.or_euler.restype = c_int
-        L.or_euler.argtypes = [c_void_p, c_int, c_int]
-        L.or_cell_residual.argtypes = [c_void_p, c_int, c_int, c_int, _dp]
-        L.or_residual.restype = c_double
-        L.or_residual.argtypes = [c_void_p, c_int, _dp]
-        L.or_mass_correct.argtypes = [c_void_p]
-        L.or_fas_cycle.restype = c_int
-        L.or_fas_cycle.argtypes = [c_void_p, _dp]
-        L.or_solve.restype = c_int
-        L.or_solve.argtypes = [c_void_p, c_double, c_int, POINTER(c_int), _dp]
-        L.or_fields.argtypes = [c_void_p, _dp]
-        L.or_two_grid_setup.restype = c_int
-        L.or_two_grid_setup.argtypes = [c_void_p, c_int]
-        L.or_two_grid_update.restype = c_int
-        L.or_two_grid_update.argtypes = [c_void_p, c_int]
-        _lib = L
+        _lib = bind(ctypes.CDLL(build()))
     return _lib
+
+
+def bind(L):
+    """Declare the argument and result types of the oracle's C functions on a loaded library."""
+    L.or_create.restype = c_void_p
+    L.or_create.argtypes = [POINTER(OrConfig)]
+    L.or_destroy.argtypes = [c_void_p]
+    for name in ("or_level_nx", "or_level_ny"):
+        getattr(L, name).restype = c_int
+        getattr(L, name).argtypes = [c_void_p, c_int]
+    L.or_c_m1.restype = c_double
+    L.or_c_m1.argtypes = [c_void_p]
+    L.or_nmom.restype = c_int
+    L.or_nmom.argtypes = [c_int]
+    L.or_alphas.argtypes = [c_int, POINTER(c_int)]
+    L.or_hermite_max_root.restype = c_double
+    L.or_hermite_max_root.argtypes = [c_int]
+    L.or_transform.argtypes = [c_int, _dp, _dp, _dp, _dp]
+    L.or_xi_mul.argtypes = [c_int, c_int, _dp, _dp, _dp]
+    L.or_macros.argtypes = [c_int, _dp, _dp, _dp]
+    L.or_cell_fields.argtypes = [c_int, _dp, _dp, _dp]
+    L.or_halfrange.argtypes = [c_int, c_int, _dp]
+    L.or_hll_flux.argtypes = [c_int, c_double, c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.or_wall_flux.argtypes = [c_int, _dp, c_double, c_double, c_int, _dp, _dp, _dp, _dp]
+    L.or_collision.argtypes = [c_int, c_int, c_double, c_double, c_double, c_double, _dp, _dp, _dp]
+    L.or_set_state.argtypes = [c_void_p, c_int, _dp, _dp]
+    L.or_get_state.argtypes = [c_void_p, c_int, _dp, _dp]
+    L.or_set_rhs.argtypes = [c_void_p, c_int, _dp, _dp]
+    L.or_get_rhs.argtypes = [c_void_p, c_int, _dp, _dp]
+    L.or_get_saved.argtypes = [c_void_p, c_int, _dp, _dp]
+    L.or_mass.restype = c_double
+    L.or_mass.argtypes = [c_void_p]
+    L.or_res0.restype = c_double
+    L.or_res0.argtypes = [c_void_p]
+    L.or_sweep.restype = c_int
+    L.or_sweep.argtypes = [c_void_p, c_int, c_int]
+    L.or_smooth.restype = c_int
+    L.or_smooth.argtypes = [c_void_p, c_int, c_int]
+    L.or_euler.restype = c_int
+    L.or_euler.argtypes = [c_void_p, c_int, c_int]
+    L.or_cell_residual.argtypes = [c_void_p, c_int, c_int, c_int, _dp]
+    L.or_residual.restype = c_double
+    L.or_residual.argtypes = [c_void_p, c_int, _dp]
+    L.or_mass_correct.argtypes = [c_void_p]
+    L.or_fas_cycle.restype = c_int
+    L.or_fas_cycle.argtypes = [c_void_p, _dp]
+    L.or_solve.restype = c_int
+    L.or_solve.argtypes = [c_void_p, c_double, c_int, POINTER(c_int), _dp]
+    L.or_fields.argtypes = [c_void_p, _dp]
+    L.or_two_grid_setup.restype = c_int
+    L.or_two_grid_setup.argtypes = [c_void_p, c_int]
+    L.or_two_grid_update.restype = c_int
+    L.or_two_grid_update.argtypes = [c_void_p, c_int]
+    L.or_slope.restype = c_double
+    L.or_slope.argtypes = [c_int, c_double, c_double, c_double, c_double]
+    L.or_face_state.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, _dp, _dp]
+    return L
 
 
 def _p(a: np.ndarray):
@@ -179,6 +191,12 @@ def wall_flux(M, uw, thw, chi, w, pc, pf, ff):
     return F
 
 
+def slope(kind, qm, q0, qp, h):
+    """Slope of one quantity from its values in three consecutive cells of width h along an
+    axis (kind 1: central difference; kind 2: van Albada average)."""
+    return lib().or_slope(kind, qm, q0, qp, h)
+
+
 def collision(M, model, Kn, Pr, omega, beta, pc, f):
     Q = np.zeros(nmom(M))
     lib().or_collision(M, model, Kn, Pr, omega, beta, _p(_arr(pc)), _p(_arr(f)), _p(Q))
@@ -241,6 +259,13 @@ class Solver:
         P, F = np.zeros((ny * nx, 4)), np.zeros((ny * nx, self.n))
         self.L.or_get_saved(self.h, level, _p(P), _p(F))
         return P, F
+
+    def face_state(self, level, i, j, ax, sd):
+        """Reconstructed state of cell (i, j) on its face sd (+1 east/north, -1 west/south) of
+        axis ax (0 x, 1 y): params [4] and coefficients [N_M] in the face basis."""
+        p, f = np.zeros(4), np.zeros(self.n)
+        self.L.or_face_state(self.h, level, i, j, ax, sd, _p(p), _p(f))
+        return p, f
 
     def sweep(self, level, k):
         return self.L.or_sweep(self.h, level, k)

@@ -31,12 +31,17 @@
  * says so at the function:
  *   - interior numerical flux: HLL form of the regularized operator
  *     P_M xi P_M (the paper defers to an external reference)  -- parity with
- *     the paper's own flux is UNPINNED; the flux is pinned only to its own
- *     definition (consistency, conservation, Maxwellian fixed point);
+ *     the paper's own flux is UNPINNED; the flux is pinned to its own
+ *     definition (consistency, upwind limits, conservation, Maxwellian fixed
+ *     point, and in its middle branch the intermediate-state form of the HLL
+ *     flux and its Rusanov special case);
  *   - Maxwell wall: kinetic half-range flux with zero wall mass flux  --
  *     parity with the paper's own boundary condition is UNPINNED; pinned to
  *     velocity-space quadrature of that reading;
  *   - limited slope: van Albada average (the paper prints central slopes);
+ *     pinned to its defining properties (central slope for equal one-sided
+ *     differences, zero for opposite ones and at a flat side, symmetry,
+ *     convexity, Sweby's limiter function, second-order accuracy);
  *   - the "correction" applied after each NMG step: total-mass rescaling --
  *     parity UNPINNED (the paper names it only by reference);
  *   - local norm of R_ij: weighted L2 norm of F_M, weight alpha! theta^-|alpha|
@@ -451,6 +456,10 @@ static double slope_of(int kind, double qm, double q0, double qp, double h) {
   return ((b * b + OR_VA_EPS2) * a + (a * a + OR_VA_EPS2) * b) / ((a * a + b * b + 2.0 * OR_VA_EPS2) * h);
 }
 
+/* the slope of one coefficient from its three cell values along an axis (kind 1 central, */
+/* 2 van Albada), exposed so that tests can check it against its defining properties      */
+double or_slope(int kind, double qm, double q0, double qp, double h) { return slope_of(kind, qm, q0, qp, h); }
+
 /* face state of cell (i,j) of level L on side sd (+1: east/north face, -1: west/south) of axis ax */
 static void face_state(const or_solver *S, const or_level *L, int i, int j, int ax, int sd, double *p, double *f) {
   int n = S->n;
@@ -472,6 +481,11 @@ static void face_state(const or_solver *S, const or_level *L, int i, int j, int 
     double g = slope_of(S->c.slope, L->F[(size_t)cm * n + o], L->F[(size_t)c * n + o], L->F[(size_t)cp * n + o], h);
     f[o] = f[o] + sd * (0.5 * h) * g;
   }
+}
+
+/* face state of cell (i, j) of level l on side sd of axis ax (params p[4], coefficients f) */
+void or_face_state(const or_solver *S, int l, int i, int j, int ax, int sd, double *p, double *f) {
+  face_state(S, &S->lev[l], i, j, ax, sd, p, f);
 }
 
 /* ------------------------------------------------------------------ */
@@ -957,23 +971,22 @@ static int prolong_update(or_solver *S, int lf) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Algorithm 2: one step of the (k+1)-level NMG iteration on level k.  */
+/* The coarse problem of Algorithm 2 built from fine level lf:         */
+/*   R_bar_h = r_h - R_h(f_bar_h) in each fine cell's basis (the       */
+/*   defect; eq. coarse-grid-problem with r_h projected in);           */
+/*   f_bar_H = I f_bar_h and R_bar_H = I R_bar_h (restriction);        */
+/*   r_H = R_H(f_bar_H) + R_bar_H, in the basis of f_bar_H.            */
 /* ------------------------------------------------------------------ */
-static int nmg(or_solver *S, int k) {
-  const or_config *cf = &S->c;
-  if (k == 0) return or_smooth(S, 0, cf->s3); /* coarsest solver: s3 FS steps */
-  int st = or_smooth(S, k, cf->s1);           /* pre-smoothing */
-  or_level *Lf = &S->lev[k], *Lc = &S->lev[k - 1];
-  /* defect R_bar = r - R(f_bar) in the fine basis */
+static void two_grid_setup(or_solver *S, int lf) {
+  or_level *Lf = &S->lev[lf], *Lc = &S->lev[lf - 1];
   double R[OR_MAXN];
   for (int j = 0; j < Lf->ny; ++j)
     for (int i = 0; i < Lf->nx; ++i) {
-      or_cell_residual(S, k, i, j, R);
+      or_cell_residual(S, lf, i, j, R);
       for (int o = 0; o < S->n; ++o) Lf->D[(size_t)(j * Lf->nx + i) * S->n + o] = -R[o];
     }
   /* f_bar_H = I f_bar, R_bar_H = I R_bar (stored in rF for now) */
-  restrict_level(S, k);
-  /* r_H = R_H(f_bar_H) + R_bar_H, in the basis of f_bar_H */
+  restrict_level(S, lf);
   Lc->has_r = 0;
   for (int j = 0; j < Lc->ny; ++j)
     for (int i = 0; i < Lc->nx; ++i) {
@@ -983,6 +996,16 @@ static int nmg(or_solver *S, int k) {
     }
   for (size_t q = 0; q < (size_t)Lc->nx * Lc->ny * S->n; ++q) Lc->rF[q] = Lc->D[q] + Lc->rF[q];
   Lc->has_r = 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2: one step of the (k+1)-level NMG iteration on level k.  */
+/* ------------------------------------------------------------------ */
+static int nmg(or_solver *S, int k) {
+  const or_config *cf = &S->c;
+  if (k == 0) return or_smooth(S, 0, cf->s3); /* coarsest solver: s3 FS steps */
+  int st = or_smooth(S, k, cf->s1);           /* pre-smoothing */
+  two_grid_setup(S, k);                        /* f_bar_H, R_bar_H and r_H */
   for (int g = 0; g < cf->gamma; ++g) {
     int e = nmg(S, k - 1);
     if (e != OR_OK) st = e;
@@ -1049,23 +1072,7 @@ void or_fields(const or_solver *S, double *out) {
 /* expose the restriction / coarse right-hand side / update for tests:  */
 /* builds level lf-1 from level lf exactly as Algorithm 2 does          */
 int or_two_grid_setup(or_solver *S, int lf) {
-  or_level *Lf = &S->lev[lf], *Lc = &S->lev[lf - 1];
-  double R[OR_MAXN];
-  for (int j = 0; j < Lf->ny; ++j)
-    for (int i = 0; i < Lf->nx; ++i) {
-      or_cell_residual(S, lf, i, j, R);
-      for (int o = 0; o < S->n; ++o) Lf->D[(size_t)(j * Lf->nx + i) * S->n + o] = -R[o];
-    }
-  restrict_level(S, lf);
-  Lc->has_r = 0;
-  for (int j = 0; j < Lc->ny; ++j)
-    for (int i = 0; i < Lc->nx; ++i) {
-      int c = j * Lc->nx + i;
-      cell_R(S, Lc, i, j, R);
-      for (int o = 0; o < S->n; ++o) Lc->D[(size_t)c * S->n + o] = R[o];
-    }
-  for (size_t q = 0; q < (size_t)Lc->nx * Lc->ny * S->n; ++q) Lc->rF[q] = Lc->D[q] + Lc->rF[q];
-  Lc->has_r = 1;
+  two_grid_setup(S, lf);
   return OR_OK;
 }
 
