@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -116,6 +116,7 @@ def bind(L):
     L.or_two_grid_setup.argtypes = [c_void_p, c_int]
     L.or_two_grid_update.restype = c_int
     L.or_two_grid_update.argtypes = [c_void_p, c_int]
+    L.or_set_threads.argtypes = [c_void_p, c_int]
     L.or_slope.restype = c_double
     L.or_slope.argtypes = [c_int, c_double, c_double, c_double, c_double]
     L.or_face_state.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, _dp, _dp]
@@ -259,6 +260,10 @@ class Solver:
         P, F = np.zeros((ny * nx, 4)), np.zeros((ny * nx, self.n))
         self.L.or_get_saved(self.h, level, _p(P), _p(F))
         return P, F
+
+    def set_threads(self, n):
+        """n > 1: OpenMP mode with n threads (the same results bit for bit); 0 or 1: serial."""
+        self.L.or_set_threads(self.h, int(n))
 
     def face_state(self, level, i, j, ax, sd):
         """Reconstructed state of cell (i, j) on its face sd (+1 east/north, -1 west/south) of

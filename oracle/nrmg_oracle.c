@@ -47,6 +47,13 @@
  *   - local norm of R_ij: weighted L2 norm of F_M, weight alpha! theta^-|alpha|
  *     -- pinned up to a constant factor by quadrature.
  *
+ * OpenMP mode (or_set_threads, n > 1; used only to time the oracle on many
+ * cores): a sweep takes its cells by anti-diagonals of its own visiting order,
+ * the cells of one diagonal in parallel, and the residual, restriction and
+ * coarse-grid update run their independent cells in parallel with sums kept
+ * in the serial order.  Every cell reads the same values as in the serial
+ * order, so both modes give the same results bit for bit (tested).
+ *
  * Units are nondimensional (m_* = 1).  Multi-indices alpha, |alpha| <= M, are
  * enumerated in graded order: |alpha| ascending, then alpha_1 descending, then
  * alpha_2 descending.  A cell state is (u_1, u_2, u_3, theta) plus N_M
@@ -334,6 +341,7 @@ typedef struct {
   double m0;    /* reference total mass */
   double res0;  /* ||R(f^0)|| of the finest level */
   int have_res0;
+  int threads;  /* > 1: the OpenMP mode (same results, bit for bit); otherwise serial */
   or_level lev[OR_MAXLEV];
 } or_solver;
 
@@ -397,6 +405,9 @@ void or_destroy(or_solver *S) {
   }
   free(S);
 }
+
+/* n > 1 selects the OpenMP mode with n threads (results identical to the serial mode) */
+void or_set_threads(or_solver *S, int n) { S->threads = n; }
 
 int or_level_nx(const or_solver *S, int l) { return S->lev[l].nx; }
 int or_level_ny(const or_solver *S, int l) { return S->lev[l].ny; }
@@ -786,7 +797,36 @@ static int cell_update(or_solver *S, or_level *L, int i, int j) {
 
 /* Directional sweep Dk, k = 1..4 (Sec. 3.1): the outer loop runs over  */
 /* i, the inner over j, ascending or descending as listed there.       */
+/* OpenMP mode of the sweep: the cells of Dk taken by anti-diagonals ii + jj = d of the    */
+/* sweep's own index order, the cells of one diagonal in parallel.  The stencil of R_ij is */
+/* a cross (no diagonal neighbours), so a neighbour on a smaller diagonal is one the       */
+/* serial order visits earlier and one on a larger diagonal one it visits later: every      */
+/* cell reads exactly the values the serial sweep gives it, and the result is the same    */
+/* bit for bit.                                                                             */
+static int sweep_by_diagonals(or_solver *S, int l, int k) {
+  or_level *L = &S->lev[l];
+  int idesc = (k == 2 || k == 3), jdesc = (k == 3 || k == 4);
+  int st = OR_OK;
+  for (int d = 0; d <= L->nx + L->ny - 2; ++d) {
+    int lo = d - (L->ny - 1) > 0 ? d - (L->ny - 1) : 0;
+    int hi = d < L->nx - 1 ? d : L->nx - 1;
+#pragma omp parallel for num_threads(S->threads) schedule(dynamic, 1)
+    for (int ii = lo; ii <= hi; ++ii) {
+      int jj = d - ii;
+      int i = idesc ? L->nx - 1 - ii : ii;
+      int j = jdesc ? L->ny - 1 - jj : jj;
+      int s = cell_update(S, L, i, j);
+      if (s != OR_OK) {
+#pragma omp atomic write
+        st = s;
+      }
+    }
+  }
+  return st;
+}
+
 int or_sweep(or_solver *S, int l, int k) {
+  if (S->threads > 1) return sweep_by_diagonals(S, l, k);
   or_level *L = &S->lev[l];
   int idesc = (k == 2 || k == 3), jdesc = (k == 3 || k == 4);
   int st = OR_OK;
@@ -871,6 +911,21 @@ double or_residual(const or_solver *S, int l, double *Rout) {
   const or_level *L = &S->lev[l];
   double R[OR_MAXN];
   double acc = 0.0;
+  if (S->threads > 1) {
+    /* OpenMP mode: the cells' terms in parallel, summed in the serial order */
+    int nc = L->nx * L->ny;
+    double *term = (double *)malloc(sizeof(double) * (size_t)nc);
+#pragma omp parallel for num_threads(S->threads) schedule(dynamic, 4)
+    for (int c = 0; c < nc; ++c) {
+      double Rc[OR_MAXN];
+      or_cell_residual(S, l, c % L->nx, c / L->nx, Rc);
+      if (Rout) memcpy(Rout + (size_t)c * S->n, Rc, S->n * sizeof(double));
+      term[c] = local_norm2(S, L->P + 4 * c, Rc) * L->dx * L->dy;
+    }
+    for (int c = 0; c < nc; ++c) acc += term[c];
+    free(term);
+    return sqrt(acc / (S->c.lx * S->c.ly));
+  }
   for (int j = 0; j < L->ny; ++j)
     for (int i = 0; i < L->nx; ++i) {
       int c = j * L->nx + i;
@@ -893,9 +948,10 @@ static void restrict_level(or_solver *S, int lf) {
   or_level *Lf = &S->lev[lf], *Lc = &S->lev[lf - 1];
   const basis_t *b = basis(S->c.M);
   int n = S->n;
-  double tf[OR_MAXN], tr[OR_MAXN];
+#pragma omp parallel for num_threads(S->threads) if (S->threads > 1) schedule(dynamic, 1)
   for (int J = 0; J < Lc->ny; ++J)
     for (int I = 0; I < Lc->nx; ++I) {
+      double tf[OR_MAXN], tr[OR_MAXN];
       int C = J * Lc->nx + I;
       int fi[4] = {(2 * J) * Lf->nx + 2 * I, (2 * J) * Lf->nx + 2 * I + 1, (2 * J + 1) * Lf->nx + 2 * I,
                    (2 * J + 1) * Lf->nx + 2 * I + 1};
@@ -954,16 +1010,20 @@ static void restrict_level(or_solver *S, int lf) {
 static int prolong_update(or_solver *S, int lf) {
   or_level *Lf = &S->lev[lf], *Lc = &S->lev[lf - 1];
   int n = S->n, st = OR_OK;
-  double tb[OR_MAXN], tt[OR_MAXN], g[OR_MAXN], pn[4], fn[OR_MAXN];
+#pragma omp parallel for num_threads(S->threads) if (S->threads > 1) schedule(dynamic, 1)
   for (int j = 0; j < Lf->ny; ++j)
     for (int i = 0; i < Lf->nx; ++i) {
+      double tb[OR_MAXN], tt[OR_MAXN], g[OR_MAXN], pn[4], fn[OR_MAXN];
       int c = j * Lf->nx + i, C = (j / 2) * Lc->nx + i / 2;
       double *pc = Lf->P + 4 * c, *fc = Lf->F + (size_t)c * n;
       or_transform(S->c.M, Lc->bP + 4 * C, pc, Lc->bF + (size_t)C * n, tb);
       or_transform(S->c.M, Lc->P + 4 * C, pc, Lc->F + (size_t)C * n, tt);
       for (int o = 0; o < n; ++o) g[o] = (fc[o] - tb[o]) + tt[o];
       int s = regrad(S, pc, g, pn, fn);
-      if (s != OR_OK) st = s;
+      if (s != OR_OK) {
+#pragma omp atomic write
+        st = s;
+      }
       memcpy(pc, pn, 4 * sizeof(double));
       memcpy(fc, fn, n * sizeof(double));
     }
@@ -979,17 +1039,20 @@ static int prolong_update(or_solver *S, int lf) {
 /* ------------------------------------------------------------------ */
 static void two_grid_setup(or_solver *S, int lf) {
   or_level *Lf = &S->lev[lf], *Lc = &S->lev[lf - 1];
-  double R[OR_MAXN];
+#pragma omp parallel for num_threads(S->threads) if (S->threads > 1) schedule(dynamic, 1)
   for (int j = 0; j < Lf->ny; ++j)
     for (int i = 0; i < Lf->nx; ++i) {
+      double R[OR_MAXN];
       or_cell_residual(S, lf, i, j, R);
       for (int o = 0; o < S->n; ++o) Lf->D[(size_t)(j * Lf->nx + i) * S->n + o] = -R[o];
     }
   /* f_bar_H = I f_bar, R_bar_H = I R_bar (stored in rF for now) */
   restrict_level(S, lf);
   Lc->has_r = 0;
+#pragma omp parallel for num_threads(S->threads) if (S->threads > 1) schedule(dynamic, 1)
   for (int j = 0; j < Lc->ny; ++j)
     for (int i = 0; i < Lc->nx; ++i) {
+      double R[OR_MAXN];
       int c = j * Lc->nx + i;
       cell_R(S, Lc, i, j, R);
       for (int o = 0; o < S->n; ++o) Lc->D[(size_t)c * S->n + o] = R[o];
