@@ -262,10 +262,13 @@ nrmg_status nrmg_fs_profile(nrmg_ctx *ctx, double *ms, long long *launches, long
  * the status word) lives in one file-scope device array of 16 MiB
  * (NRMG_NOALLOC_SCRATCH_BYTES) that every GPU loading the library holds until exit; the call
  * makes no cudaMalloc/cudaFree and no allocating library call.  Sizes: the call fits when
- * cells * (4 + N_M rounded up to 4) * 8 bytes plus about 80 KB of tables fit in 16 MiB
- * (e.g. 128x128 at M = 5, 64x64 at M = 10); larger problems return NRMG_ERR_OOM before any
- * GPU work.  The first call on a device looks up the array's device address on that device
- * (cudaGetSymbolAddress) and must come before any stream capture.  Every call shares the
+ * cells * (5 + N_M rounded up to 4) * 8 bytes (params, padded coefficients and theta^(1-omega)
+ * of every cell) plus at most 160 KB of index and wall tables, reduction partials and 256-byte
+ * alignment fit in 16 MiB (e.g. 128x128 at M = 5, 64x64 at M = 10); larger problems return
+ * NRMG_ERR_OOM before any GPU work.  Each call looks up the array's device address on the
+ * current device (cudaGetSymbolAddress, with that device current; the device of the state
+ * pointers must be the current one); the first call on a device loads the library's device
+ * code there and should come before any stream capture.  Every call shares the
  * array and it keeps the last call's contents; calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialized by the caller.  Synchronizes the stream.
  * Errors: NRMG_ERR_ARG (as nrmg_create), NRMG_ERR_OOM (too large), NRMG_ERR_NONPHYSICAL,

@@ -1508,19 +1508,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NRMG_NOALLOC_SC
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-void *g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
-
-// Device address of the scratch array on the current device; looked up once per device.
-cudaError_t noalloc_scratch(int dev, void **out) {
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+// Device address of the scratch array on the current device.  In host code the array's name
+// is only a host-side stand-in, so the address is looked up with the device current; it is
+// looked up on every call (no allocation, no cache shared between host threads, and still
+// right after the device's context was reset).
+cudaError_t noalloc_scratch(void **out) {
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = p;
   return cudaSuccess;
 }
 
@@ -1567,7 +1563,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   int dev = 0, nsm = 0;
   void *base = nullptr;
   if (cudaGetDevice(&dev) != cudaSuccess) return NRMG_ERR_CUDA;
-  if (noalloc_scratch(dev, &base) != cudaSuccess) return NRMG_ERR_CUDA;
+  if (noalloc_scratch(&base) != cudaSuccess) return NRMG_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NRMG_ERR_CUDA;
   char *b = (char *)base;
 

@@ -473,11 +473,22 @@ def residual_noalloc(prob, params, coeffs, want_R=True, stream=None):
         wa[k].u = (c_double * 3)(*w.u)
         wa[k].theta = w.theta
         wa[k].chi = w.chi
-    R = torch.empty((prob.nx * prob.ny, nmom(prob.M)), dtype=torch.float64, device=coeffs.device) if want_R else None
+    ncell, n = prob.nx * prob.ny, nmom(prob.M)
+    # the library reads params[ncell][4] and coeffs[ncell][N_M] blindly: check them here
+    for name, t, cols in (("params", params, 4), ("coeffs", coeffs, n)):
+        if tuple(t.shape) != (ncell, cols):
+            raise ValueError(f"{name} must have shape ({ncell}, {cols}), got {tuple(t.shape)}")
+    if params.device != coeffs.device or not coeffs.is_cuda:
+        raise ValueError("params and coeffs must be on the same CUDA device")
+    dev = coeffs.device
+    R = torch.empty((ncell, n), dtype=torch.float64, device=dev) if want_R else None
     norm = c_double(0.0)
-    s = stream if stream is not None else torch.cuda.current_stream(coeffs.device)
-    st = L.nrmg_residual_noalloc(ctypes.byref(grid), prob.M, prob.Kn, wa, ctypes.byref(coll), ctypes.byref(opts),
-                                 _ptr(params), _ptr(coeffs), _ptr(R), ctypes.byref(norm), c_void_p(s.cuda_stream))
+    # the library takes its scratch address and SM count from the current device
+    with torch.cuda.device(dev):
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        st = L.nrmg_residual_noalloc(ctypes.byref(grid), prob.M, prob.Kn, wa, ctypes.byref(coll),
+                                     ctypes.byref(opts), _ptr(params), _ptr(coeffs), _ptr(R), ctypes.byref(norm),
+                                     c_void_p(s.cuda_stream))
     if st != OK:
         raise NrmgError(st, "nrmg_residual_noalloc")
     return R, norm.value

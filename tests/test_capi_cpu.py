@@ -151,3 +151,35 @@ def test_net_and_learned_entry_points_check_arguments():
     L.nrmg_set_state_from_fields.argtypes = [c_void_p, c_void_p]
     assert L.nrmg_set_state_from_fields(None, None) == nrmg.ERR_ARG
     assert L.nrmg_mixed_fallback(None) == 0
+
+
+def test_noalloc_binding_checks_shapes_before_the_library():
+    """residual_noalloc hands the library bare pointers: arrays of the wrong shape or on
+    different devices are refused on the host."""
+    import torch
+
+    from inputs import lid_cavity
+
+    prob = lid_cavity(16, 5, 0.1, 0.2)
+    for P, F in ((torch.zeros(4, 4, dtype=torch.float64), torch.zeros(256, 56, dtype=torch.float64)),
+                 (torch.zeros(256, 4, dtype=torch.float64), torch.zeros(256, 55, dtype=torch.float64)),
+                 (torch.zeros(256, 4, dtype=torch.float64), torch.zeros(256, 56, dtype=torch.float64))):
+        with pytest.raises(ValueError):
+            nrmg.residual_noalloc(prob, P, F)
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    """The sweep-grid cache: a stored result is found again under the same key (problem
+    shapes sorted, scheme and model in the key), and writes replace the file atomically."""
+    path = str(tmp_path / "tune.json")
+
+    class O:
+        order, slope, precision = 2, 2, 0
+
+    key = "GB300/152sm|" + ";".join(sorted(["64x64:M5:L4", "128x128:M8:L5"])) + "|order2:slope2:prec0|model0"
+    nrmg._tune_store(path, key, 2, {1: 0.5, 2: 0.4})
+    nrmg._tune_store(path, key + "x", 3, {3: 0.1})
+    data = nrmg._tune_load(path)
+    assert data[key]["ctas_per_sm"] == 2 and data[key]["s_per_cycle"] == {"1": 0.5, "2": 0.4}
+    assert data[key + "x"]["ctas_per_sm"] == 3
+    assert nrmg._tune_load(str(tmp_path / "missing.json")) == {}

@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 import torch
 
-from inputs import heated_cavity, lid_cavity, random_state
+from conftest import oracle_solver
+from inputs import ESBGK, Wall, heated_cavity, lid_cavity, maxwellian_state, random_state
 from paper_2206_13164_gb300 import nrmg
 
 pytestmark = pytest.mark.gpu
@@ -58,10 +59,42 @@ def test_noalloc_repeated_call_same_state_is_stable():
         assert _rel(R1, R0) <= 1e-12 and abs(n1 - n0) <= 1e-12 * n0
 
 
+@pytest.mark.parametrize("case", ["partial_accommodation", "esbgk", "no_R_out"])
+def test_noalloc_matches_the_oracle(case):
+    """Partial accommodation (chi < 1) on every wall, the ES-BGK model, and a call that asks for
+    the norm only (no residual rows): against the CPU oracle and the workspace path."""
+    torch.cuda.set_device(0)
+    if case == "partial_accommodation":
+        prob = lid_cavity(24, 6, 0.1, 0.3, order=2, slope=2)
+        prob = prob.replace(walls=[Wall(theta=w.theta, u=w.u, chi=0.6) for w in prob.walls])
+    elif case == "esbgk":
+        prob = lid_cavity(16, 8, 0.1, 0.3, order=2, slope=2, model=ESBGK, beta=2.0 / 3.0)
+    else:
+        prob = heated_cavity(16, 5, 0.05, order=2, slope=2)
+    rng = np.random.default_rng(9)
+    Pn, Fn = random_state(rng, prob.ny, prob.nx, prob.M, amp=0.05)
+    S = oracle_solver(prob)
+    S.set_state(prob.levels - 1, Pn, Fn)
+    Ro, no = S.residual()
+    P, F = _T(Pn), _T(Fn)
+    R0, n0 = _existing(prob, P, F)
+    for _ in range(2):
+        R1, n1 = nrmg.residual_noalloc(prob, P, F, want_R=(case != "no_R_out"))
+        assert abs(n1 - no) <= 1e-12 * no and abs(n1 - n0) <= 1e-12 * n0
+        if case == "no_R_out":
+            assert R1 is None
+        else:
+            assert np.abs(R1.cpu().numpy() - Ro).max() <= 1e-12 * np.abs(Ro).max()
+            assert _rel(R1, R0) <= 1e-12
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
+    """A 256x256, M = 10 state (150 MB of coefficients) does not fit the 16 MiB scratch: the
+    call returns NRMG_ERR_OOM before any GPU work (the tensors have the problem's shape, so the
+    library never sees arrays smaller than it was told)."""
     prob = lid_cavity(256, 10, 0.01, 0.5, order=2, slope=2)
-    P = torch.zeros((4, 4), dtype=torch.float64, device=DEV)  # never read: the size check comes first
-    F = torch.zeros((4, 286), dtype=torch.float64, device=DEV)
+    P, F = maxwellian_state(256, 256, 10)
+    P, F = _T(P), _T(F)
     with pytest.raises(nrmg.NrmgError) as e:
         nrmg.residual_noalloc(prob, P, F)
     assert e.value.status == nrmg.ERR_OOM
