@@ -141,6 +141,16 @@ nrmg_status nrmg_set_state(nrmg_ctx *ctx, int level, const double *dev_params, c
 /* Copy level `level`'s state out to device arrays (either may be NULL). */
 nrmg_status nrmg_get_state(nrmg_ctx *ctx, int level, double *dev_params, double *dev_coeffs);
 
+/* The same two calls with HOST arrays (same dense layout: params [cells][4], coefficients
+ * [cells][N_M]), for callers whose state lives in host memory.  Each array moves with one
+ * cudaMemcpyAsync / cudaMemcpy2DAsync on the context's stream (the coefficient rows go
+ * straight into their padded device rows); page-locked host memory makes the copies
+ * asynchronous DMA.  nrmg_set_state_host then checks the state as nrmg_set_state does and
+ * synchronizes; nrmg_get_state_host synchronizes before it returns (either pointer may be
+ * NULL).  Errors as nrmg_set_state / nrmg_get_state. */
+nrmg_status nrmg_set_state_host(nrmg_ctx *ctx, int level, const double *host_params, const double *host_coeffs);
+nrmg_status nrmg_get_state_host(nrmg_ctx *ctx, int level, double *host_params, double *host_coeffs);
+
 /* Set the right-hand side r of level `level` (the r of Algorithm 1),
  * expanded in the per-cell bases dev_rparams; NULL pointers clear it (r = 0).
  * Algorithm 2 overwrites the r of every level below the finest.  Synchronizes.
@@ -249,6 +259,11 @@ nrmg_status nrmg_set_profiling(nrmg_ctx *ctx, int on);
 nrmg_status nrmg_fs_profile_levels(nrmg_ctx *ctx, double *ms_per_level, long long *updates_per_level);
 nrmg_status nrmg_fs_profile(nrmg_ctx *ctx, double *ms, long long *launches, long long *updates_no_r,
                             long long *updates_r);
+/* The residual kernel's record (every mode: norms, defects, coarse right-hand sides), kept
+ * while profiling is on (at most 16384 launches): summed event time in ms, timed launches,
+ * and the cells evaluated without and with a right-hand side r; synchronizes, then resets. */
+nrmg_status nrmg_residual_profile(nrmg_ctx *ctx, double *ms, long long *launches, long long *cells_no_r,
+                                  long long *cells_r);
 
 /* Residual without any device allocation.  The paper has no counterpart: this entry point is
  * for callers that cannot allocate device memory themselves (for example code running under

@@ -352,6 +352,11 @@ struct nrmg_ctx {
   std::vector<int> ev_level;
   std::vector<int> ev_prec;   // 0 FP64 sweep, 1 FP32 correction sweep
   size_t ev_used;
+  // event timing of residual launches (all modes)
+  std::vector<cudaEvent_t> rev;
+  std::vector<long long> rev_cells;
+  std::vector<int> rev_hasr;
+  size_t rev_used;
   char err[256];
 };
 
@@ -536,7 +541,15 @@ nrmg_status residual(nrmg_ctx *ctx, int level, int mode, double *out, int out_st
   LevelDev L = ctx->lev[level];
   if (mode == kResCoarseRhs) L.has_r = 0;
   int g = grid_for(ctx, 1, L.ncell);
+  bool timed = ctx->profiling && ctx->rev_used + 2 <= ctx->rev.size();
+  if (timed) CK(cudaEventRecord(ctx->rev[ctx->rev_used], ctx->stream));
   CK(launch_residual(ctx->K, L, mode, out, out_stride, ctx->partials, g, ctx->stream));
+  if (timed) {
+    CK(cudaEventRecord(ctx->rev[ctx->rev_used + 1], ctx->stream));
+    ctx->rev_cells[ctx->rev_used / 2] = L.ncell;
+    ctx->rev_hasr[ctx->rev_used / 2] = L.has_r;
+    ctx->rev_used += 2;
+  }
   ctx->launches += 1;
   if (grid_out) *grid_out = g;
   return NRMG_OK;
@@ -882,6 +895,27 @@ nrmg_status nrmg_get_state(nrmg_ctx *ctx, int level, double *P, double *F) {
   return NRMG_OK;
 }
 
+nrmg_status nrmg_set_state_host(nrmg_ctx *ctx, int level, const double *host_P, const double *host_F) {
+  if (!ctx || level < 0 || level >= ctx->levels || !host_P || !host_F) return NRMG_ERR_ARG;
+  LevelDev &L = ctx->lev[level];
+  // one copy per array; the coefficient rows land in their padded device rows directly
+  CK(cudaMemcpyAsync(L.P, host_P, sizeof(double) * 4 * L.ncell, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpy2DAsync(L.F, sizeof(double) * ctx->NP, host_F, sizeof(double) * ctx->N, sizeof(double) * ctx->N,
+                       L.ncell, cudaMemcpyHostToDevice, ctx->stream));
+  return finish_state(ctx, level);
+}
+
+nrmg_status nrmg_get_state_host(nrmg_ctx *ctx, int level, double *host_P, double *host_F) {
+  if (!ctx || level < 0 || level >= ctx->levels) return NRMG_ERR_ARG;
+  LevelDev &L = ctx->lev[level];
+  if (host_P) CK(cudaMemcpyAsync(host_P, L.P, sizeof(double) * 4 * L.ncell, cudaMemcpyDeviceToHost, ctx->stream));
+  if (host_F)
+    CK(cudaMemcpy2DAsync(host_F, sizeof(double) * ctx->N, L.F, sizeof(double) * ctx->NP, sizeof(double) * ctx->N,
+                         L.ncell, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return NRMG_OK;
+}
+
 nrmg_status nrmg_set_rhs(nrmg_ctx *ctx, int level, const double *rP, const double *rF) {
   if (!ctx || level < 0 || level >= ctx->levels) return NRMG_ERR_ARG;
   LevelDev &L = ctx->lev[level];
@@ -1081,9 +1115,38 @@ nrmg_status nrmg_set_profiling(nrmg_ctx *ctx, int on) {
     ctx->ev_hasr.assign(n / 2, 0);
     ctx->ev_level.assign(n / 2, 0);
     ctx->ev_prec.assign(n / 2, 0);
+    const size_t nr = 2 * 16384;
+    ctx->rev.resize(nr);
+    for (size_t k = 0; k < nr; ++k) CK(cudaEventCreate(&ctx->rev[k]));
+    ctx->rev_cells.assign(nr / 2, 0);
+    ctx->rev_hasr.assign(nr / 2, 0);
   }
   ctx->profiling = on ? 1 : 0;
   ctx->ev_used = 0;
+  ctx->rev_used = 0;
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_residual_profile(nrmg_ctx *ctx, double *ms, long long *launches, long long *cells_no_r,
+                                  long long *cells_r) {
+  if (!ctx) return NRMG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  double tot = 0.0;
+  long long c0 = 0, c1 = 0;
+  for (size_t k = 0; k + 1 < ctx->rev_used; k += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->rev[k], ctx->rev[k + 1]));
+    tot += t;
+    if (ctx->rev_hasr[k / 2])
+      c1 += ctx->rev_cells[k / 2];
+    else
+      c0 += ctx->rev_cells[k / 2];
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = (long long)(ctx->rev_used / 2);
+  if (cells_no_r) *cells_no_r = c0;
+  if (cells_r) *cells_r = c1;
+  ctx->rev_used = 0;
   return NRMG_OK;
 }
 

@@ -107,6 +107,12 @@ def lib():
         L.nrmg_fs_profile.restype = c_int
         L.nrmg_fs_profile.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
                                       POINTER(c_longlong)]
+        L.nrmg_residual_profile.restype = c_int
+        L.nrmg_residual_profile.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_longlong),
+                                            POINTER(c_longlong)]
+        for name in ("nrmg_set_state_host", "nrmg_get_state_host"):
+            getattr(L, name).restype = c_int
+            getattr(L, name).argtypes = [c_void_p, c_int, c_void_p, c_void_p]
         L.nrmg_fs_profile_levels.restype = c_int
         L.nrmg_fs_profile_levels.argtypes = [c_void_p, POINTER(c_double), POINTER(c_longlong)]
         L.nrmg_peak_fma.restype = c_int
@@ -144,6 +150,19 @@ def _status_name(s: int) -> str:
 
 def nmom(M: int) -> int:
     return (M + 1) * (M + 2) * (M + 3) // 6
+
+
+def _host_ptr(t, cols):
+    """Address of a host float64 array with `cols` columns (torch CPU tensor or numpy)."""
+    if isinstance(t, torch.Tensor):
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.shape[-1] != cols:
+            raise ValueError(f"expected a contiguous float64 host tensor with {cols} columns")
+        return c_void_p(t.data_ptr())
+    import numpy as np
+
+    if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"] or t.shape[-1] != cols:
+        raise ValueError(f"expected a contiguous float64 host array with {cols} columns")
+    return c_void_p(t.ctypes.data)
 
 
 def _ptr(t):
@@ -224,6 +243,19 @@ class Solver:
         F = torch.empty((ny * nx, self.N), dtype=torch.float64, device=self.device)
         self._check(self.L.nrmg_get_state(self.ctx, level, _ptr(P), _ptr(F)), "nrmg_get_state")
         return P, F
+
+    def set_state_host(self, params, coeffs, level=None):
+        """State from host arrays (float64, contiguous, [cells,4] and [cells,N_M]; pinned
+        memory gives asynchronous copies)."""
+        level = self.levels - 1 if level is None else level
+        self._check(self.L.nrmg_set_state_host(self.ctx, level, _host_ptr(params, 4), _host_ptr(coeffs, self.N)),
+                    "nrmg_set_state_host")
+
+    def get_state_host(self, params, coeffs, level=None):
+        """Copy the state into host arrays (float64, contiguous); synchronizes."""
+        level = self.levels - 1 if level is None else level
+        self._check(self.L.nrmg_get_state_host(self.ctx, level, _host_ptr(params, 4), _host_ptr(coeffs, self.N)),
+                    "nrmg_get_state_host")
 
     def set_rhs(self, level, rparams=None, rcoeffs=None):
         self._check(self.L.nrmg_set_rhs(self.ctx, level, _ptr(rparams), _ptr(rcoeffs)), "nrmg_set_rhs")
@@ -341,6 +373,13 @@ class Solver:
         up = (c_longlong * self.levels)()
         self._check(self.L.nrmg_fs_profile_levels(self.ctx, ms, up), "nrmg_fs_profile_levels")
         return [(ms[l], up[l]) for l in range(self.levels)]
+
+    def residual_profile(self):
+        """(ms, launches, cells without r, cells with r) of the timed residual launches."""
+        ms, n, c0, c1 = c_double(0.0), c_longlong(0), c_longlong(0), c_longlong(0)
+        self._check(self.L.nrmg_residual_profile(self.ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(c0),
+                                                 ctypes.byref(c1)), "nrmg_residual_profile")
+        return ms.value, n.value, c0.value, c1.value
 
     def fs_profile(self):
         """(ms, launches, cell updates without r, cell updates with r) of the timed FS launches."""
