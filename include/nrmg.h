@@ -298,8 +298,10 @@ nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, double Kn, const
  * level: every FS stage of all problems (pre-smoothing at one depth together with the
  * coarsest solves reached there, or post-smoothing at one depth) is ONE persistent launch
  * whose work queue merges the problems' exact-order schedules by earliest start, so small
- * problems share the GPU.  Contexts must have the same M, order, slope, s1, s2, s3, model,
- * gamma = 1 and precision 0; grids, Kn and walls may differ.  All batch work is issued on
+ * problems share the GPU.  Contexts must have the same order, slope, s1, s2, s3, model,
+ * gamma = 1 and precision 0; grids, M, Kn and walls may differ (the launch sizes its shared
+ * memory for the largest M, and a CTA loads the index tables of an item's M when it changes).
+ * All batch work is issued on
  * the first context's stream.  The caller owns the batch workspace (>= 256-byte aligned,
  * size from nrmg_batch_workspace_bytes, 0 when the contexts are incompatible); the batch
  * keeps pointers to the contexts, which must outlive it.  Per-problem results follow

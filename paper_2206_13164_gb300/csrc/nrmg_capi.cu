@@ -1223,6 +1223,7 @@ struct nrmg_batch {
   };
   std::vector<Stage> down, up;  // down[d]: depth d pre-smoothing / coarsest; up[d]: depth d post
   int *ctl;                     // device: [0] item counter, [1] abort word
+  int kmax;                     // the context of the largest M (shared-memory layout, occupancy)
   int grid;
   int depth;
   long long launches;
@@ -1243,7 +1244,7 @@ bool batch_compatible(nrmg_ctx *const *c, int n) {
   for (int b = 0; b < n; ++b) {
     if (!c[b]) return false;
     const nrmg_opts &o = c[b]->opts, &o0 = c[0]->opts;
-    if (c[b]->M != c[0]->M || o.order != o0.order || o.slope != o0.slope || o.s1 != o0.s1 || o.s2 != o0.s2 ||
+    if (o.order != o0.order || o.slope != o0.slope || o.s1 != o0.s1 || o.s2 != o0.s2 ||
         o.s3 != o0.s3 || o.gamma != 1 || o.precision != 0 || c[b]->coll.model != c[0]->coll.model)
       return false;
   }
@@ -1324,7 +1325,7 @@ nrmg_status batch_fs(nrmg_batch *B, nrmg_batch::Stage &S) {
   }
   CK(cudaMemsetAsync(B->ctl, 0, sizeof(int), B->stream));
   long long g = std::min<long long>(B->grid, S.nitems);
-  Consts K0 = B->ctx[0]->K;  // layout and tables (same M for the whole batch), batch abort word
+  Consts K0 = B->ctx[B->kmax]->K;  // the largest M: shared-memory size and first tables
   K0.abort_flag = B->ctl + 1;
   CK(launch_fs_batch(S.desc, S.items, S.nitems, B->ctl, K0, (int)g, B->stream));
   B->launches += 1;
@@ -1424,7 +1425,10 @@ nrmg_status nrmg_batch_create(nrmg_ctx *const *ctxs, int n, void *dev_workspace,
   int D = 0;
   for (int b = 0; b < n; ++b) D = std::max(D, ctxs[b]->levels - 1);
   B->depth = D;
-  B->grid = ctxs[0]->nsm * std::max(1, ctxs[0]->occ[0]);
+  B->kmax = 0;
+  for (int b = 1; b < n; ++b)
+    if (ctxs[b]->M > ctxs[B->kmax]->M) B->kmax = b;
+  B->grid = ctxs[0]->nsm * std::max(1, ctxs[B->kmax]->occ[0]);
   if (cudaMemsetAsync(B->ctl, 0, 256, B->stream) != cudaSuccess) {
     delete B;
     return NRMG_ERR_CUDA;
@@ -1548,7 +1552,7 @@ nrmg_status nrmg_batch_solve(nrmg_batch *B, double tol, int max_cycles, int *cyc
 int nrmg_batch_graph(const nrmg_batch *B) { return B && B->graph_state == 1 ? 1 : 0; }
 
 nrmg_status nrmg_batch_set_grid(nrmg_batch *B, int ctas_per_sm) {
-  if (!B || ctas_per_sm < 1 || ctas_per_sm > std::max(1, B->ctx[0]->occ[0])) return NRMG_ERR_ARG;
+  if (!B || ctas_per_sm < 1 || ctas_per_sm > std::max(1, B->ctx[B->kmax]->occ[0])) return NRMG_ERR_ARG;
   B->grid = B->ctx[0]->nsm * ctas_per_sm;
   return NRMG_OK;
 }

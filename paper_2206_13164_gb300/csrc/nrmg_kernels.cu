@@ -534,9 +534,13 @@ __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int 
   }
 }
 
-// FS sweeps of several problems (same M and scheme) in one persistent launch.  items[q] =
+// FS sweeps of several problems (same scheme, any M) in one persistent launch.  items[q] =
 // (problem, item of that problem's level queue); the problem descriptors (scheme constants
-// and level) are copied into shared memory per item.  All descriptors share one abort word.
+// and level) are copied into shared memory per item.  K0 is the descriptor of the largest M:
+// the dynamic shared memory is sized for it, and the working set of a smaller M fits in its
+// layout; when the next item's M differs from the one whose index tables the CTA holds, the
+// CTA rebinds its shared memory and loads that M's tables.  All descriptors share one abort
+// word.
 template <bool kES>
 __global__ void __launch_bounds__(kThreads) fs_batch_kernel(const BatchDesc *desc, const int2 *items,
                                                             long long total, int *counter, Consts K0) {
@@ -546,7 +550,7 @@ __global__ void __launch_bounds__(kThreads) fs_batch_kernel(const BatchDesc *des
   load_tables(K0, s);
   __syncthreads();
   const int tid = threadIdx.x;
-  int cur = -1;
+  int cur = -1, curM = K0.M;
   for (;;) {
     if (tid == 0) {
       int it = atomicAdd(counter, 1);
@@ -564,6 +568,13 @@ __global__ void __launch_bounds__(kThreads) fs_batch_kernel(const BatchDesc *des
       for (int w = tid; w < (int)(sizeof(BatchDesc) / sizeof(int)); w += kThreads) dst[w] = src[w];
       cur = iv.x;
       __syncthreads();
+      if (bd.K.M != curM) {  // uniform: bd is shared; the item is already in a register
+        s = bind_smem(smem_raw, bd.K.M, bd.K.N, bd.K.NP);
+        load_tables(bd.K, s);
+        curM = bd.K.M;
+        if (tid == 0) s.iarr[I_ABW] = 0;  // the control words moved with the layout
+        __syncthreads();
+      }
     }
     const int ncell = bd.L.ncell, qv = iv.y;
     const int st = qv / (4 * ncell), k = (qv / ncell) % 4, c = qv % ncell;

@@ -173,6 +173,45 @@ def _ptr(t):
     return c_void_p(t.data_ptr())
 
 
+# ---------------------------------------------------------------- autotune cache
+TUNE_CACHE = os.path.join(os.path.dirname(_build.LIB), "autotune.json")
+
+
+def _tune_load(path):
+    import json
+
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _tune_store(path, key, best, times):
+    """Record a tuning result (atomic replace, so concurrent writers never leave a torn file)."""
+    import json
+
+    data = _tune_load(path)
+    data[key] = {"ctas_per_sm": int(best), "s_per_cycle": {str(k): v for k, v in times.items()}}
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _device_tag(device):
+    p = torch.cuda.get_device_properties(device)
+    return f"{p.name}/{p.multi_processor_count}sm"
+
+
+def tune_key(device, shapes, opts, model):
+    """Cache key of a sweep-grid tuning: the GPU, the (nx, ny, M, levels) of every problem
+    (sorted), the scheme (order, slope) and precision, and the collision model."""
+    sh = ";".join(f"{nx}x{ny}:M{M}:L{lv}" for nx, ny, M, lv in sorted(shapes))
+    return f"{_device_tag(device)}|{sh}|order{opts.order}:slope{opts.slope}:prec{opts.precision}|model{model}"
+
+
 class Solver:
     """One cavity problem on the current CUDA device.
 
@@ -321,11 +360,22 @@ class Solver:
         self._check(self.L.nrmg_set_grid(self.ctx, ctas_per_sm), "nrmg_set_grid")
         self.tuned = ctas_per_sm
 
-    def autotune(self, candidates=None, reps=1):
+    def tune_key(self):
+        return tune_key(self.device, [(self.nx, self.ny, self.M, self.levels)], self.opts, self.coll.model)
+
+    def autotune(self, candidates=None, reps=1, cache=None):
         """Time `reps` FAS cycles per candidate CTAs/SM of the sweep launches (the cycles advance
-        the solution, not its fixed point) and keep the fastest.  Returns {candidate: s/cycle}."""
+        the solution, not its fixed point) and keep the fastest.  Returns {candidate: s/cycle}.
+        cache: a JSON file path (True: TUNE_CACHE) keyed by tune_key(); a cached entry is used
+        without timing (the returned dict is then the cached timings), a new result is stored."""
         import time
 
+        path = TUNE_CACHE if cache is True else cache
+        if path:
+            hit = _tune_load(path).get(self.tune_key())
+            if hit:
+                self.set_grid(hit["ctas_per_sm"])
+                return {int(k): v for k, v in hit["s_per_cycle"].items()}
         limit = int(self.L.nrmg_grid_limit(self.ctx))
         cands = [c for c in (candidates or range(1, limit + 1)) if 1 <= c <= limit]
         times = {}
@@ -339,6 +389,8 @@ class Solver:
             times[c] = (time.perf_counter() - t0) / reps
         best = min(times, key=times.get)
         self.set_grid(best)
+        if path:
+            _tune_store(path, self.tune_key(), best, times)
         return times
 
     def set_reference(self, mass=0.0, res0=0.0):
@@ -400,7 +452,7 @@ def peak_fma(precision: int = 0, iters: int = 4096, stream=None) -> float:
 
 
 class Batch:
-    """Several Solvers (same M and scheme; grids, Kn, walls may differ) cycled in lockstep with
+    """Several Solvers (same scheme; grids, M, Kn, walls may differ) cycled in lockstep with
     one persistent FS launch per stage.  All work runs on the first solver's stream."""
 
     def __init__(self, solvers):
@@ -459,11 +511,23 @@ class Batch:
         if st != OK:
             raise NrmgError(st, "nrmg_batch_set_grid")
 
-    def autotune(self, candidates=(1, 2, 3), reps=1):
+    def tune_key(self):
+        s0 = self.solvers[0]
+        return tune_key(s0.device, [(s.nx, s.ny, s.M, s.levels) for s in self.solvers], s0.opts, s0.coll.model)
+
+    def autotune(self, candidates=(1, 2, 3), reps=1, cache=None):
         """Time one batched cycle per candidate CTAs/SM (the cycles advance the solution) and
-        keep the fastest.  Returns {candidate: seconds}."""
+        keep the fastest.  Returns {candidate: seconds}.  cache: as Solver.autotune, keyed by
+        the batch's problem shapes."""
         import time
 
+        path = TUNE_CACHE if cache is True else cache
+        if path:
+            hit = _tune_load(path).get(self.tune_key())
+            if hit:
+                self.set_grid(hit["ctas_per_sm"])
+                self.tuned = hit["ctas_per_sm"]
+                return {int(k): v for k, v in hit["s_per_cycle"].items()}
         times = {}
         for c in candidates:
             try:
@@ -479,6 +543,8 @@ class Batch:
         best = min(times, key=times.get)
         self.set_grid(best)
         self.tuned = best
+        if path:
+            _tune_store(path, self.tune_key(), best, times)
         return times
 
 

@@ -450,6 +450,39 @@ def test_batch_graph_replay_equals_eager_cycles():
         assert_close(N(a.get_state()[1]), N(b.get_state()[1]), 1e-13, "coeffs")
 
 
+def test_batch_with_mixed_orders_equals_individual_cycles():
+    """One batch whose problems have different M (3, 5 and 8: shared memory sized for the
+    largest, each CTA reloading the index tables when an item's M changes), cycled eagerly and
+    then from the captured graph: every problem equals its own single-problem cycles, and
+    after the same cycles the oracle."""
+    probs = [lid_cavity(32, 5, 0.1, 0.3, order=2, slope=2, levels=3),
+             lid_cavity(16, 8, 0.2, 0.2, order=2, slope=2, levels=2),
+             lid_cavity(24, 3, 0.5, 0.1, order=2, slope=2, levels=2).replace(ny=16),
+             lid_cavity(16, 8, 0.05, 0.4, order=2, slope=2, levels=2, dtnu=1.0)]
+    st = torch.cuda.Stream()  # a non-default stream, so that the batch captures its cycle
+    with torch.cuda.stream(st):
+        single = [nrmg.from_problem(p, device=DEV, stream=st) for p in probs]
+        batched = [nrmg.from_problem(p, device=DEV, stream=st) for p in probs]
+        B = nrmg.Batch(batched)
+        for _ in range(3):
+            rb = B.fas_cycle()
+            rs = [S.fas_cycle() for S in single]
+            assert np.allclose(rb, rs, rtol=1e-12, atol=0)
+        assert B.graph
+    for Sg, Sb in zip(single, batched):
+        Pg, Fg = Sg.get_state()
+        Pb, Fb = Sb.get_state()
+        assert_close(N(Pb), N(Pg), 1e-13, "params")
+        assert_close(N(Fb), N(Fg), 1e-13, "coeffs")
+    O = oracle_solver(probs[1])
+    for _ in range(3):
+        O.fas_cycle()
+    Po, Fo = O.get_state()
+    Pb, Fb = batched[1].get_state()
+    assert_close(N(Pb), Po, 1e-11, "params vs oracle")
+    assert_close(N(Fb), Fo, 1e-11, "coeffs vs oracle")
+
+
 def test_batch_solve_matches_oracle():
     probs = _batch_problems()[:2]
     batched = [gpu(p) for p in probs]
