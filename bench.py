@@ -72,18 +72,23 @@ def batch64_instances(seed=0, count=64):
     return out
 
 
-def run_batch64(args):
+def batch_cycle_flops(inst):
+    """Algorithmic FP64 flops of the FS updates of one batched V-cycle: 4 FS steps on every
+    level, coarse levels with a right-hand side r."""
+    fl = 0
+    for w in inst:
+        for l in range(w["levels"]):
+            cells = (w["nx"] >> (w["levels"] - 1 - l)) ** 2
+            fl += 4 * 4 * cells * flops_per_update(w["M"], 2, l < w["levels"] - 1)
+    return fl
+
+
+def batch64_measure(args, dev, world=1):
+    """Batched V-cycles of the 64 cavities, timed: (record, kernel launches in the timed cycles)."""
     import torch
 
     from paper_2206_13164_gb300 import nrmg
 
-    rank, local_rank, world = dist_env()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
     inst = batch64_instances()
     stream = torch.cuda.Stream(dev)
     groups = {}
@@ -93,7 +98,8 @@ def run_batch64(args):
                             order=2, slope=2, dtnu=1.0, device=dev, stream=stream)
             groups.setdefault(w["M"], []).append((w, S))
         t0 = time.perf_counter()
-        batches = {M: nrmg.Batch([S for _, S in g]) for M, g in groups.items()}
+        # one batch of all 64 problems (both M): one persistent launch per stage
+        batches = {"all": nrmg.Batch([S for g in groups.values() for _, S in g])}
         t_build = time.perf_counter() - t0
         tune = {M: B.autotune() for M, B in batches.items()}
         for _ in range(args.warmup):
@@ -113,19 +119,48 @@ def run_batch64(args):
     launches = sum(B.launches for B in batches.values()) - l0
     upd = sum(cycle_updates(w) for w in inst) * args.steps
     ms = max_over_ranks(ms, dev)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    ach = batch_cycle_flops(inst) * args.steps / (ms * 1e-3) / 1e12
+    rec = {"value": replica_throughput(upd, world, ms * 1e-3), "unit": "cell-moment updates/s",
+           "ms_per_step": ms / args.steps, "steps": args.steps,
+           "instances": {str(M): len(g) for M, g in groups.items()},
+           "batches": len(batches), "batch_build_s": t_build,
+           "graph_replay": {str(M): B.graph for M, B in batches.items()},
+           "autotune_ctas_per_sm": {str(M): B.tuned for M, B in batches.items()},
+           "autotune_s": {str(M): t for M, t in tune.items()},
+           "roofline": {"bound": "alu", "kernel": "fs_batch_kernel; achieved = algorithmic FS flops of the "
+                                                 "batched cycle over the whole cycle's time (transfers included)",
+                        "achieved": ach, "peak": fp64_peak(nsm), "unit": "TFLOP/s", "frac": ach / fp64_peak(nsm),
+                        "peak_source": "derived FP64 pipe peak"}}
+    del batches, groups
+    torch.cuda.empty_cache()
+    return rec, launches
+
+
+def run_batch64(args):
+    import torch
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    rec, launches = batch64_measure(args, dev, world)
+    ms = rec["ms_per_step"] * args.steps
     if rank == 0:
-        out = {"metric": "cell-moment updates/s", "value": replica_throughput(upd, world, ms * 1e-3),
+        out = {"metric": "cell-moment updates/s", "value": rec["value"],
                "unit": "cell-moment updates/s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": "64 lid-driven cavities (seed 0): Kn 10^U(-2,0), lid U(0.05,0.5), N in "
-                                      "{64,128,256}, M in {5,8}, BGK, 2nd order; one batch per M, one persistent "
-                                      "FS launch per stage", "step": "one batched V-cycle of all 64 instances",
-                          "instances": {str(M): len(g) for M, g in groups.items()},
-                          "batch_build_s": t_build,
-                          "graph_replay": {str(M): B.graph for M, B in batches.items()}, "autotune_ctas_per_sm": {str(M): B.tuned for M, B in batches.items()},
-                          "autotune_s": {str(M): t for M, t in tune.items()}},
-               "gpu_launches": launches}
+                                      "{64,128,256}, M in {5,8}, BGK, 2nd order; one batch of all 64, one "
+                                      "persistent FS launch per stage", "step": "one batched V-cycle of all 64 instances",
+                          "instances": rec["instances"], "batch_build_s": rec["batch_build_s"],
+                          "graph_replay": rec["graph_replay"], "autotune_ctas_per_sm": rec["autotune_ctas_per_sm"],
+                          "autotune_s": rec["autotune_s"]},
+               "roofline": rec["roofline"], "gpu_launches": launches}
         print(json.dumps(out), flush=True)
 
 
@@ -190,9 +225,11 @@ def mirror_symmetry_error(fields):
     return float((dev[keep] / scale[keep]).max())
 
 
-def learned_time_to_tol(w, tol=1e-8, grid=0, grid_mixed=None):
+def learned_time_to_tol(w, tol=1e-8, grid=0, grid_mixed=None, dtnu=0.0, ref_fields=None):
     """Time to tol of the learned start on the workload (with and without the network, and with
-    the mixed-precision smoother), or the reason it cannot run."""
+    the mixed-precision smoother), or the reason it cannot run.  dtnu: the local-step cap of
+    every solver context, the same as the plain solve's so that the cycles compare like for
+    like; ref_fields: the plain FP64 solution, against which each form's fields are compared."""
     from paper_2206_13164_gb300 import learned
 
     if w["heat"] or not w["lid"]:
@@ -200,12 +237,15 @@ def learned_time_to_tol(w, tol=1e-8, grid=0, grid_mixed=None):
     if not os.path.exists(learned.WEIGHTS):
         return {"unavailable": "trained weights missing: " + learned.WEIGHTS}
     net = learned.Net.load(max_pixels=w["nx"] ** 2)
-    out = {"start_grid": w["nx"] // 8, "weights": os.path.relpath(learned.WEIGHTS, ROOT), "solver_dtnu": 1.0}
+    out = {"start_grid": w["nx"] // 8, "weights": os.path.relpath(learned.WEIGHTS, ROOT), "solver_dtnu": dtnu}
     for key, nn, prec in (("no_net", None, 0), ("net", net, 0), ("net_mixed", net, 1)):
-        ls = learned.LearnedSolve(w["nx"], w["M"], w["Kn"], w["lid"], start=w["nx"] // 8, net=nn, precision=prec)
+        ls = learned.LearnedSolve(w["nx"], w["M"], w["Kn"], w["lid"], start=w["nx"] // 8, net=nn, precision=prec,
+                                  dtnu=dtnu)
         ls.set_grid(grid if prec == 0 or grid_mixed is None else grid_mixed)
         r = ls.run(tol=tol)
         out[key] = {k: r[k] for k in LEARNED_KEYS}
+        if ref_fields is not None:
+            out[key]["field_rel_err"] = learned.field_rel_errors(ls.target.fields(), ref_fields)
         del ls
     return out
 
@@ -215,12 +255,19 @@ def run_learned512(args):
     residual 1e-8 (of the plain start's residual) against the plain FP64 solve."""
     import torch
 
-    from paper_2206_13164_gb300 import learned
-
     rank, local_rank, world = dist_env()
     if rank != 0:
         return
     torch.cuda.set_device(local_rank)
+    print(json.dumps(learned512_record(args, local_rank)), flush=True)
+
+
+def learned512_record(args, local_rank=0):
+    """The learned start's JSON record on the held-out 512x512 cavity."""
+    import torch
+
+    from paper_2206_13164_gb300 import learned
+
     N, M, Kn, U = 512, 10, 0.03, 0.35
     net = learned.Net.load(max_pixels=N * N)
     fwd_ms, fwd_tf = net_forward_timing(net, N, N, reps=max(args.steps, 3), warmup=max(args.warmup, 3))
@@ -249,11 +296,11 @@ def run_learned512(args):
                       "weights": os.path.relpath(learned.WEIGHTS, ROOT), "meta": getattr(net, "meta", None),
                       "autotune_ctas_per_sm": grid, "autotune_s_per_cycle": tune},
            "plain": {k: ev["plain"][k] for k in ("status", "cycles", "rel_res", "t_total")},
-           "no_net": {k: ev["no_net"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
-           "net": {k: ev["net"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
+           "no_net": {k: ev["no_net"][k] for k in LEARNED_KEYS + ("max_field_diff", "field_rel_err")},
+           "net": {k: ev["net"][k] for k in LEARNED_KEYS + ("max_field_diff", "field_rel_err")},
            "plain_mixed": {k: ev["plain_mixed"][k] for k in ("status", "cycles", "rel_res", "t_total",
-                                                             "max_field_diff")},
-           "net_mixed": {k: ev["net_mixed"][k] for k in LEARNED_KEYS + ("max_field_diff",)},
+                                                             "max_field_diff", "field_rel_err")},
+           "net_mixed": {k: ev["net_mixed"][k] for k in LEARNED_KEYS + ("max_field_diff", "field_rel_err")},
            "speedup_vs_plain": t_plain / t_net,
            "speedup_vs_plain_with_mixed_smoother": t_plain / ev["net_mixed"]["t_total"],
            "roofline": {"bound": "tensor", "kernel": "network forward (4 conv3x3 launches, mma.sync BF16)",
@@ -261,7 +308,7 @@ def run_learned512(args):
                         "traffic": None, "peak_source": src, "forward_ms": fwd_ms,
                         "flops_per_forward": net_flops(N * N)},
            "clocks": clk.summary()}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def walls_of(w):
@@ -381,9 +428,10 @@ def replica_throughput(units_per_rank, world, seconds):
     return units_per_rank * world / seconds
 
 
-def cpu_oracle_sample(w, level_shift: int, sweeps: int = 1):
-    """Time the CPU oracle (as it stands, serial) on directional sweeps D1 of one level of the
-    workload.  Returns (cell-moment updates/s, seconds, description)."""
+def cpu_oracle_sample(w, level_shift: int, sweeps: int = 1, threads: int = 0):
+    """Time the CPU oracle (as it stands: serial, or its OpenMP mode with `threads` > 1) on
+    directional sweeps D1 of one level of the workload.  Returns (cell-moment updates/s,
+    seconds, description)."""
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     import oracle
 
@@ -400,6 +448,8 @@ def cpu_oracle_sample(w, level_shift: int, sweeps: int = 1):
             c.wall_u[k][d] = u[d]
         c.wall_theta[k], c.wall_chi[k] = th, chi
     S = oracle.Solver(c)
+    if threads > 1:
+        S.set_threads(threads)
     lev = w["levels"] - 1 - level_shift
     ny, nx = S.shape(lev)
     t0 = time.perf_counter()
@@ -407,20 +457,22 @@ def cpu_oracle_sample(w, level_shift: int, sweeps: int = 1):
         S.sweep(lev, 1)
     dt = time.perf_counter() - t0
     upd = sweeps * nx * ny * nmom(w["M"])
+    mode = f"oracle OpenMP mode, {threads} threads" if threads > 1 else "serial oracle"
     return upd / dt, dt, f"{sweeps} directional sweep(s) D1 over the {nx}x{ny} level of the workload " \
-                         f"({nx * ny} cell updates), serial oracle"
+                         f"({nx * ny} cell updates), {mode}"
 
 
 def run_reference(args, w):
     rank, _, world = dist_env()
     if rank != 0:
         return
-    # each step: one D1 sweep over the second-finest level (same per-cell work as the finest)
+    # each step: one D1 sweep of the level cpu_baseline times (the finest up to 256x256)
+    shift = cpu_sample_level_shift(w)
     for _ in range(args.warmup):
-        cpu_oracle_sample(w, 1)
+        cpu_oracle_sample(w, shift)
     times, rates, desc = [], [], ""
     for _ in range(args.steps):
-        r, dt, desc = cpu_oracle_sample(w, 1)
+        r, dt, desc = cpu_oracle_sample(w, shift)
         times.append(dt)
         rates.append(r)
     tot_upd = sum(r * t for r, t in zip(rates, times))
@@ -438,6 +490,197 @@ def run_reference(args, w):
     print(json.dumps(out), flush=True)
 
 
+def workload_summary(w, args, dev, steps=3):
+    """A workload's plain V-cycle (updates/s, the FS kernel's roofline), its mixed-precision
+    cycle and both forms' seconds to 1e-8 with their field errors."""
+    import torch
+
+    from paper_2206_13164_gb300 import nrmg
+
+    props = torch.cuda.get_device_properties(dev)
+
+    def make(prec=0, dtnu=0.0):
+        return nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
+                           Pr=w["Pr"], order=w["order"], slope=w["slope"], precision=prec, dtnu=dtnu, device=dev)
+
+    S = make()
+    for _ in range(args.warmup):
+        S.fas_cycle()
+    tune = S.autotune(candidates=(1, 2, 3), reps=1)
+    S.set_profiling(True)
+    S.fs_profile()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(S.stream)
+    for _ in range(steps):
+        S.fas_cycle()
+    e1.record(S.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    fs_ms, fs_n, u0, u1 = S.fs_profile()
+    S.set_profiling(False)
+    grid = S.tuned
+    del S
+    torch.cuda.empty_cache()
+    fl = u0 * flops_per_update(w["M"], w["order"], False) + u1 * flops_per_update(w["M"], w["order"], True)
+    ach = fl / (fs_ms * 1e-3) / 1e12
+    peak = fp64_peak(props.multi_processor_count)
+    rec = {"workload": w["desc"], "value": cycle_updates(w) * steps / (ms * 1e-3), "unit": "cell-moment updates/s",
+           "ms_per_step": ms / steps, "steps": steps, "autotune_ctas_per_sm": grid, "autotune_s_per_cycle": tune,
+           "roofline": {"bound": "alu", "kernel": "fs_kernel (persistent FS sweep, all levels)", "achieved": ach,
+                        "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "fs_ms_per_step": fs_ms / steps,
+                        "peak_source": "derived FP64 pipe peak"}}
+    mixed, mgrid = mixed_cycle_timing(w, make, args, dev, props, 1, lambda: None, steps=steps)
+    rec["mixed"] = mixed
+    rec["time_to_tol"] = time_to_tol(w, make, dev, grid, mgrid, learned_forms=False)
+    return rec
+
+
+def extra_workloads(args, dev):
+    """The other configurations, each in its own sub-object: the bottom-heated 512x512 Shakhov
+    cavity (plain and mixed, mirror symmetry), the batch of 64 cavities, and the learned start
+    on the held-out 512x512 cavity.  A failure is reported in place of that record."""
+    import torch
+
+    out = {}
+    for name in ("heat512", "batch64", "learned512"):
+        t0 = time.perf_counter()
+        try:
+            if name == "heat512":
+                out[name] = workload_summary(WORKLOADS["heat512"], args, dev)
+            elif name == "batch64":
+                bargs = argparse.Namespace(steps=min(args.steps, 3), warmup=min(args.warmup, 2))
+                rec, launches = batch64_measure(bargs, dev)
+                rec["gpu_launches"] = launches
+                rec["workload"] = ("64 lid-driven cavities (seed 0): Kn 10^U(-2,0), lid U(0.05,0.5), N in "
+                                   "{64,128,256}, M in {5,8}, BGK, 2nd order, local step capped at 1/nu; one "
+                                   "persistent FS launch per stage for all 64")
+                out[name] = rec
+            else:
+                out[name] = learned512_record(args)
+        except Exception as e:  # report, keep the main line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    return out
+
+
+def fp64_peak(nsm):
+    """Derived FP64 pipe peak in TFLOP/s: SMs x 2 DFMA/clk x 2 flops x 2070 MHz."""
+    return nsm * 2 * 2 * 2.07e9 / 1e12
+
+
+# executed FP64 flops per cell update of the FS kernel (2 x DFMA + DADD + DMUL thread
+# instructions per update, ncu, finest-level launch of the 64x64 M=10 second-order cavity):
+# the algorithmic count (flops_per_update) is 1.22x this
+FS_EXECUTED_FLOPS = {10: 50340}
+
+
+def mixed_cycle_timing(w, make, args, dev, props, world, barrier, steps=None):
+    """The V-cycle with the mixed-precision smoother: ms per cycle, updates/s and the FP32
+    correction sweep's roofline.  Returns (record, tuned grid)."""
+    import torch
+
+    steps = steps or args.steps
+    S2 = make(1)
+    for _ in range(args.warmup):
+        S2.fas_cycle()
+    tune_mixed = S2.autotune(reps=1)
+    S2.set_profiling(True)
+    S2.fs_profile()
+    barrier()
+    torch.cuda.synchronize(dev)
+    m0 = torch.cuda.Event(enable_timing=True)
+    m1 = torch.cuda.Event(enable_timing=True)
+    m0.record(S2.stream)
+    for _ in range(steps):
+        S2.fas_cycle()
+    m1.record(S2.stream)
+    torch.cuda.synchronize(dev)
+    mms = m0.elapsed_time(m1)
+    mlev = S2.fs_profile_levels()
+    cms, cn, cu0, cu1 = S2.fs_profile()
+    S2.set_profiling(False)
+    corr_fl = (cu0 + cu1) * flops_per_corr_update(w["M"], w["order"])
+    fp32_peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    rec = {"value": cycle_updates(w) * steps * world / (mms * 1e-3), "unit": "cell-moment updates/s",
+           "ms_per_step": mms / steps, "steps": steps, "dtype": "f32 correction sweeps + f64 defect/transfers",
+           "roofline": {"bound": "alu", "kernel": "fs_corr_kernel (FP32 correction sweeps, FS timings "
+                                                 "of all levels; the coarsest level stays FP64)",
+                        "achieved": corr_fl / (cms * 1e-3) / 1e12 if cms > 0 else None,
+                        "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": (corr_fl / (cms * 1e-3) / 1e12 / fp32_peak) if cms > 0 else None,
+                        "peak_source": "derived: SMs x 128 FFMA/clk x 2 flops x 2070 MHz",
+                        "flops_per_cell_update": flops_per_corr_update(w["M"], w["order"]),
+                        "sweep_ms_per_step": cms / steps,
+                        "sweep_ms_per_step_by_level": [round(m / steps, 3) for m, _ in mlev]},
+           "autotune_ctas_per_sm": S2.tuned, "autotune_s_per_cycle": tune_mixed}
+    grid = S2.tuned
+    del S2
+    torch.cuda.empty_cache()
+    return rec, grid
+
+
+def time_to_tol(w, make, dev, grid, grid_mixed, learned_forms=True, tol=1e-8):
+    """Seconds and cycles to relative residual tol from the global Maxwellian: plain FP64,
+    mixed precision and (lid cavities) the learned start, every form with the same local
+    step; each form's fields against the plain FP64 solution (per-field max relative error),
+    and the mirror asymmetry of the bottom-heated cavity."""
+    import torch
+
+    from paper_2206_13164_gb300 import learned
+
+    ttt = {"tol": tol, "solver_dtnu": 0.0}
+    ref = None
+    for prec, key in ((0, "plain_fp64"), (1, "mixed")):
+        S3 = make(prec)
+        S3.set_grid(grid if prec == 0 or grid_mixed is None else grid_mixed)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st, cyc, rr = S3.solve(tol, 400)
+        torch.cuda.synchronize(dev)
+        ttt[key] = {"seconds": time.perf_counter() - t0, "cycles": cyc, "rel_residual": rr, "status": int(st)}
+        f = S3.fields()
+        if prec == 0:
+            ref = f
+        else:
+            ttt[key]["field_rel_err_vs_plain_fp64"] = learned.field_rel_errors(f, ref)
+            ttt[key]["fell_back_to_fp64"] = bool(S3.mixed_fallback())
+        if w["heat"]:
+            ttt[key]["mirror_symmetry_rel_err"] = mirror_symmetry_error(f)
+        del S3, f
+        torch.cuda.empty_cache()
+    ttt["mixed_over_plain_time"] = ttt["mixed"]["seconds"] / ttt["plain_fp64"]["seconds"]
+    if learned_forms:
+        ttt["learned"] = learned_time_to_tol(w, grid=grid, grid_mixed=grid_mixed, dtnu=0.0, ref_fields=ref)
+        if "net" in ttt["learned"]:
+            ttt["learned_over_plain_time"] = ttt["learned"]["net"]["t_total"] / ttt["plain_fp64"]["seconds"]
+            ttt["learned_mixed_over_plain_time"] = (ttt["learned"]["net_mixed"]["t_total"]
+                                                    / ttt["plain_fp64"]["seconds"])
+    return ttt
+
+
+def cpu_sample_level_shift(w):
+    """The level the CPU oracle is timed on: the finest up to 256x256, else the next one."""
+    return 0 if w["nx"] <= 256 else 1
+
+
+def cpu_baseline(w):
+    """The oracle as it stands on the host: serial (1 core), and its OpenMP mode on all cores,
+    each on one D1 sweep of the same level of the workload."""
+    shift = cpu_sample_level_shift(w)
+    r, dt, desc = cpu_oracle_sample(w, shift)
+    out = {"value": r, "unit": "cell-moment updates/s", "cores": 1, "kind": "oracle",
+           "sample": desc + f" ({dt:.1f} s)"}
+    ncores = os.cpu_count() or 1
+    if ncores > 1:
+        ro, dto, desco = cpu_oracle_sample(w, shift, threads=ncores)
+        out["openmp"] = {"value": ro, "unit": "cell-moment updates/s", "cores": ncores, "kind": "oracle",
+                         "sample": desco + f" ({dto:.1f} s)", "speedup_over_serial": ro / r}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,6 +692,8 @@ def main():
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the two solves to 1e-8")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision cycle timing")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-start solves to 1e-8")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (heated 512x512, batch of 64, held-out learned 512x512)")
     args = ap.parse_args()
     if args.workload == "learned512":
         if args.impl == "reference":
@@ -482,8 +727,11 @@ def main():
         if world > 1:
             dist.barrier()
 
-    S = nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
-                    Pr=w["Pr"], order=w["order"], slope=w["slope"], device=dev)
+    def make(prec=0, dtnu=0.0):
+        return nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
+                           Pr=w["Pr"], order=w["order"], slope=w["slope"], precision=prec, dtnu=dtnu, device=dev)
+
+    S = make()
     stream = S.stream
     fp64_peak_meas = nrmg.peak_fma(0, 2048, stream)
     for _ in range(args.warmup):
@@ -498,6 +746,7 @@ def main():
         gpu_id = str(local_rank)
     S.set_profiling(True)
     S.fs_profile()  # reset
+    S.residual_profile()
     l0 = S.launches
     with ClockSampler(gpu_id) as clk:
         barrier()
@@ -515,35 +764,31 @@ def main():
     launches = S.launches - l0
     per_level = S.fs_profile_levels()
     fs_ms, fs_n, u0, u1 = S.fs_profile()
+    res_ms, res_n, rc0, rc1 = S.residual_profile()
     S.set_profiling(False)
     ms = max_over_ranks(ms, dev)
     upd = cycle_updates(w) * args.steps
     value = replica_throughput(upd, world, ms * 1e-3)
 
-    # end to end through the public API: pinned host state -> device, one cycle, state -> host
+    # end to end through the public C ABI with HOST buffers: every step copies the state from
+    # pinned host memory into the solver (nrmg_set_state_host), runs one cycle and reads the
+    # state back (nrmg_get_state_host); the copies are inside the timed region
     P, F = S.get_state()
     hP = torch.empty(P.shape, dtype=P.dtype, pin_memory=True)
     hF = torch.empty(F.shape, dtype=F.dtype, pin_memory=True)
     hP.copy_(P)
     hF.copy_(F)
-    dP, dF = torch.empty_like(P), torch.empty_like(F)
     oP = torch.empty(P.shape, dtype=P.dtype, pin_memory=True)
     oF = torch.empty(F.shape, dtype=F.dtype, pin_memory=True)
+    del P, F
     e2e_steps = max(1, min(args.steps, 5))
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with torch.cuda.stream(stream):
-            dP.copy_(hP, non_blocking=True)
-            dF.copy_(hF, non_blocking=True)
-        S.set_state(dP, dF)
+        S.set_state_host(hP, hF)
         S.fas_cycle()
-        P2, F2 = S.get_state()
-        with torch.cuda.stream(stream):
-            oP.copy_(P2, non_blocking=True)
-            oF.copy_(F2, non_blocking=True)
-        torch.cuda.synchronize(dev)
+        S.get_state_host(oP, oF)
     e2e_s = time.perf_counter() - t0
     barrier()
     e2e_s = max_over_ranks(e2e_s, dev)
@@ -553,80 +798,30 @@ def main():
     # mixed precision: FP32 correction sweeps inside FP64 defect correction, same cycle
     mixed, mixed_grid = None, 0
     if not args.no_mixed:
-        S2 = nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
-                         Pr=w["Pr"], order=w["order"], slope=w["slope"], precision=1, device=dev)
-        for _ in range(args.warmup):
-            S2.fas_cycle()
-        tune_mixed = S2.autotune(reps=1)
-        S2.set_profiling(True)
-        S2.fs_profile()
-        barrier()
-        torch.cuda.synchronize(dev)
-        m0 = torch.cuda.Event(enable_timing=True)
-        m1 = torch.cuda.Event(enable_timing=True)
-        m0.record(S2.stream)
-        for _ in range(args.steps):
-            S2.fas_cycle()
-        m1.record(S2.stream)
-        torch.cuda.synchronize(dev)
-        mms = m0.elapsed_time(m1)
-        mlev = S2.fs_profile_levels()
-        cms, cn, cu0, cu1 = S2.fs_profile()
-        S2.set_profiling(False)
-        corr_fl = (cu0 + cu1) * flops_per_corr_update(w["M"], w["order"])
-        fp32_peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
-        mixed = {"value": cycle_updates(w) * args.steps * world / (mms * 1e-3), "unit": "cell-moment updates/s",
-                 "ms_per_step": mms / args.steps, "dtype": "f32 correction sweeps + f64 defect/transfers",
-                 "roofline": {"bound": "alu", "kernel": "fs_corr_kernel (FP32 correction sweeps, FS timings "
-                                                       "of all levels; the coarsest level stays FP64)",
-                              "achieved": corr_fl / (cms * 1e-3) / 1e12 if cms > 0 else None,
-                              "peak": fp32_peak, "unit": "TFLOP/s",
-                              "frac": (corr_fl / (cms * 1e-3) / 1e12 / fp32_peak) if cms > 0 else None,
-                              "peak_source": "derived: SMs x 128 FFMA/clk x 2 flops x 2070 MHz",
-                              "flops_per_cell_update": flops_per_corr_update(w["M"], w["order"]),
-                              "sweep_ms_per_step": cms / args.steps,
-                              "sweep_ms_per_step_by_level": [round(m / args.steps, 3) for m, _ in mlev]}}
-        mixed_grid = S2.tuned
-        mixed["autotune_ctas_per_sm"] = S2.tuned
-        mixed["autotune_s_per_cycle"] = tune_mixed
-        del S2
+        mixed, mixed_grid = mixed_cycle_timing(w, make, args, dev, props, world, barrier)
 
-    # time to relative residual 1e-8 from the global Maxwellian, plain FP64 vs mixed
+    # time to relative residual 1e-8 from the global Maxwellian, plain FP64 vs mixed vs learned
     ttt = None
     if world == 1 and not args.no_time_to_tol:
-        ttt = {"tol": 1e-8}
-        for prec, key in ((0, "plain_fp64"), (1, "mixed")):
-            S3 = nrmg.Solver(w["nx"], w["nx"], w["M"], w["Kn"], walls_of(w), levels=w["levels"], model=w["model"],
-                             Pr=w["Pr"], order=w["order"], slope=w["slope"], precision=prec, device=dev)
-            S3.set_grid(S.tuned if prec == 0 or mixed is None else mixed_grid)
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            st, cyc, rr = S3.solve(1e-8, 400)
-            torch.cuda.synchronize(dev)
-            ttt[key] = {"seconds": time.perf_counter() - t0, "cycles": cyc, "rel_residual": rr,
-                        "status": int(st)}
-            if w["heat"]:
-                ttt[key]["mirror_symmetry_rel_err"] = mirror_symmetry_error(S3.fields())
-            del S3
-        ttt["mixed_over_plain_time"] = ttt["mixed"]["seconds"] / ttt["plain_fp64"]["seconds"]
-        if not args.no_learned:
-            ttt["learned"] = learned_time_to_tol(w, grid=S.tuned, grid_mixed=mixed_grid if mixed else None)
-            if "net" in ttt["learned"]:
-                ttt["learned_over_plain_time"] = ttt["learned"]["net"]["t_total"] / ttt["plain_fp64"]["seconds"]
+        ttt = time_to_tol(w, make, dev, S.tuned, mixed_grid if mixed else None,
+                          learned_forms=not args.no_learned)
 
     # roofline of the dominant kernel (the persistent FS sweep kernel, all levels)
     fl = u0 * flops_per_update(w["M"], w["order"], False) + u1 * flops_per_update(w["M"], w["order"], True)
     achieved = fl / (fs_ms * 1e-3) / 1e12 if fs_ms > 0 else None
     nsm = props.multi_processor_count
-    peak_nominal = nsm * 2 * 2 * 2.07e9 / 1e12  # 2 DFMA/clk/SM x 2 flops x 2070 MHz
+    peak_nominal = fp64_peak(nsm)
+    res_fl = rc0 * flops_per_update(w["M"], w["order"], False) + rc1 * flops_per_update(w["M"], w["order"], True)
+    res_ach = res_fl / (res_ms * 1e-3) / 1e12 if res_ms > 0 else None
     clocks = clk.summary()
+    plain_grid = S.tuned
+    del S
+    torch.cuda.empty_cache()
 
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            r, dt, desc = cpu_oracle_sample(w, 0 if w["nx"] <= 256 else 1)
-            cpu = {"value": r, "unit": "cell-moment updates/s", "cores": 1, "kind": "oracle",
-                   "sample": desc + f" ({dt:.1f} s)"}
+            cpu = cpu_baseline(w)
         out = {
             "metric": "cell-moment updates/s", "value": value, "unit": "cell-moment updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -636,7 +831,7 @@ def main():
                        "l2": "inputs larger than L2 (finest-level coefficient array alone is "
                              f"{w['nx'] ** 2 * ((nmom(w['M']) + 3) // 4 * 4) * 8 / 1e6:.0f} MB)",
                        "parallelism": f"replicas x{world}", "rel_residual_after": rel,
-                       "autotune_ctas_per_sm": S.tuned, "autotune_s_per_cycle": tune_plain},
+                       "autotune_ctas_per_sm": plain_grid, "autotune_s_per_cycle": tune_plain},
             "roofline": {"bound": "alu", "kernel": "fs_kernel (persistent FS sweep, all levels)",
                          "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                          "frac": (achieved / peak_nominal) if achieved else None,
@@ -649,15 +844,27 @@ def main():
                          "fs_ms_per_step_by_level": [round(m / args.steps, 3) for m, _ in per_level],
                          "fs_us_per_cell_update_by_level": [round(1e3 * m / u, 3) if u else None
                                                             for m, u in per_level],
-                         "flops_per_cell_update": flops_per_update(w["M"], w["order"], False)},
+                         "flops_per_cell_update": flops_per_update(w["M"], w["order"], False),
+                         "executed_flops_per_cell_update_ncu": FS_EXECUTED_FLOPS.get(w["M"])},
+            "residual_roofline": {"bound": "alu", "kernel": "residual_kernel (norms, defects, coarse right-hand "
+                                                            "sides of the timed cycles)",
+                                  "achieved": res_ach, "peak": peak_nominal, "unit": "TFLOP/s",
+                                  "frac": (res_ach / peak_nominal) if res_ach else None,
+                                  "ms_per_step": res_ms / args.steps, "launches": res_n,
+                                  "cells": rc0 + rc1, "flops_per_cell": flops_per_update(w["M"], w["order"], False),
+                                  "peak_source": "derived FP64 pipe peak, as above"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "cell-moment updates/s", "h2d_bytes_per_step": bytes_state,
-                    "d2h_bytes_per_step": bytes_state, "steps": e2e_steps},
+                    "d2h_bytes_per_step": bytes_state, "steps": e2e_steps,
+                    "path": "nrmg_set_state_host (pinned host -> device) + nrmg_fas_cycle + nrmg_get_state_host "
+                            "(device -> pinned host), one C ABI call each"},
             "gpu_launches": launches,
             "clocks": clocks,
             "mixed": mixed,
             "time_to_tol": ttt,
         }
+        if world == 1 and not args.no_extras and args.workload == "lid256":
+            out["extra_workloads"] = extra_workloads(args, dev)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -407,6 +407,17 @@ def train(net, data, epochs, batch=16, lr=2e-3, lr_min=2e-5, wd=1e-4, seed=0, lo
     return hist
 
 
+FIELD_NAMES = ("rho", "u1", "u2", "u3", "theta", "s11", "s12", "s13", "s22", "s23", "s33", "q1", "q2", "q3")
+
+
+def field_rel_errors(f, ref):
+    """Per field of nrmg_fields' [ny][nx][14] layout: max |f - ref| / max |ref| (fields whose
+    reference vanishes, such as u3, are left out)."""
+    dev = (f - ref).abs().amax(dim=(0, 1))
+    scale = ref.abs().amax(dim=(0, 1))
+    return {n: float(dev[k] / scale[k]) for k, n in enumerate(FIELD_NAMES) if float(scale[k]) > 1e-12}
+
+
 def evaluate(N, M, Kn, U, net, start=64, polish=2, decide=2, tol=1e-8, grid=0, mixed=False):
     """Cycles and wall time to tol on one cavity: plain start, climb without the network, climb
     with it (and, with mixed, the plain start and the climb with the network on the
@@ -417,7 +428,9 @@ def evaluate(N, M, Kn, U, net, start=64, polish=2, decide=2, tol=1e-8, grid=0, m
     out = {"N": N, "M": M, "Kn": Kn, "U": U, "start": start, "grid": grid, "plain": rp}
     if mixed:
         pm, rpm = plain_solve(N, M, Kn, U, tol, grid=grid, precision=1)
-        rpm["max_field_diff"] = float((pm.fields() - ref).abs().max())
+        fpm = pm.fields()
+        rpm["max_field_diff"] = float((fpm - ref).abs().max())
+        rpm["field_rel_err"] = field_rel_errors(fpm, ref)
         out["plain_mixed"] = rpm
         pm.close()
     runs = [("no_net", None, 0), ("net", net, 0)] + ([("net_mixed", net, 1)] if mixed else [])
@@ -425,7 +438,9 @@ def evaluate(N, M, Kn, U, net, start=64, polish=2, decide=2, tol=1e-8, grid=0, m
         ls = LearnedSolve(N, M, Kn, U, start=start, net=nn, precision=prec)
         ls.set_grid(grid)
         r = ls.run(tol=tol, polish=polish, decide=decide)
-        r["max_field_diff"] = float((ls.target.fields() - ref).abs().max())
+        fl = ls.target.fields()
+        r["max_field_diff"] = float((fl - ref).abs().max())
+        r["field_rel_err"] = field_rel_errors(fl, ref)
         out[name] = r
         del ls
     plain.close()
