@@ -51,6 +51,9 @@ class OrConfig(ctypes.Structure):
         ("s1", c_int), ("s2", c_int), ("s3", c_int), ("gamma", c_int),
         ("wall_u", (c_double * 3) * 4), ("wall_theta", c_double * 4), ("wall_chi", c_double * 4),
         ("dtnu", c_double),
+        # widths of the finest level's columns [nx] and rows [ny] (NULL: uniform grid); read
+        # by or_create only
+        ("hx", POINTER(c_double)), ("hy", POINTER(c_double)),
     ]
 
 

@@ -322,11 +322,16 @@ typedef struct {
   double wall_theta[4];
   double wall_chi[4];
   double dtnu; /* > 0: local time step capped at dtnu / nu (0: the CFL step alone) */
+  /* non-uniform grid (Sec. 2.4: the local time step serves non-uniform grids): the widths of
+   * the finest level's columns hx[nx] and rows hy[ny], summing to lx and ly; NULL: uniform */
+  const double *hx, *hy;
 } or_config;
 
 typedef struct {
   int nx, ny;
-  double dx, dy;
+  double dx, dy;      /* uniform widths (lx / nx, ly / ny) */
+  double *hx, *hy;    /* width of each column and row (all dx, dy on a uniform grid) */
+  int uniform;
   double *P, *F;     /* state: [cell][4], [cell][n] */
   double *rP, *rF;   /* right-hand side r and the basis it is expanded in */
   int has_r;
@@ -361,7 +366,7 @@ static void set_maxwellian(or_solver *S, int l) {
 static double total_mass(const or_solver *S, int l) {
   const or_level *L = &S->lev[l];
   double m = 0.0;
-  for (int c = 0; c < L->nx * L->ny; ++c) m += L->F[(size_t)c * S->n] * L->dx * L->dy;
+  for (int c = 0; c < L->nx * L->ny; ++c) m += L->F[(size_t)c * S->n] * L->hx[c % L->nx] * L->hy[c / L->nx];
   return m;
 }
 
@@ -383,6 +388,15 @@ or_solver *or_create(const or_config *cfg) {
     }
     L->dx = cfg->lx / L->nx;
     L->dy = cfg->ly / L->ny;
+    L->hx = (double *)malloc(sizeof(double) * L->nx);
+    L->hy = (double *)malloc(sizeof(double) * L->ny);
+    L->uniform = !(cfg->hx && cfg->hy);
+    /* the finest level takes the given widths; a coarse cell merges two columns (rows) of the
+     * next finer level, whose widths add */
+    for (int i = 0; i < L->nx; ++i)
+      L->hx[i] = L->uniform ? L->dx : (sh == 0 ? cfg->hx[i] : S->lev[l + 1].hx[2 * i] + S->lev[l + 1].hx[2 * i + 1]);
+    for (int j = 0; j < L->ny; ++j)
+      L->hy[j] = L->uniform ? L->dy : (sh == 0 ? cfg->hy[j] : S->lev[l + 1].hy[2 * j] + S->lev[l + 1].hy[2 * j + 1]);
     size_t nc = (size_t)L->nx * L->ny;
     L->P = (double *)calloc(nc * 4, sizeof(double));
     L->F = (double *)calloc(nc * S->n, sizeof(double));
@@ -394,6 +408,7 @@ or_solver *or_create(const or_config *cfg) {
     set_maxwellian(S, l);
   }
   S->m0 = total_mass(S, cfg->levels - 1);
+  S->c.hx = S->c.hy = NULL; /* copied into the levels; the caller's arrays may go */
   return S;
 }
 
@@ -402,6 +417,7 @@ void or_destroy(or_solver *S) {
   for (int l = 0; l < S->c.levels; ++l) {
     or_level *L = &S->lev[l];
     free(L->P); free(L->F); free(L->rP); free(L->rF); free(L->bP); free(L->bF); free(L->D);
+    free(L->hx); free(L->hy);
   }
   free(S);
 }
@@ -460,11 +476,25 @@ double or_mass(const or_solver *S) { return total_mass(S, S->c.levels - 1); }
 /* A cell whose neighbour along the axis is a wall gets zero slope     */
 /* along that axis (the paper is silent there).                        */
 /* ------------------------------------------------------------------ */
+/* van Albada et al. (1982) smooth limited average of the one-sided differences a, b of a cell
+ * of width h, as a slope */
+static double va_slope(double a, double b, double h) {
+  return ((b * b + OR_VA_EPS2) * a + (a * a + OR_VA_EPS2) * b) / ((a * a + b * b + 2.0 * OR_VA_EPS2) * h);
+}
+
 static double slope_of(int kind, double qm, double q0, double qp, double h) {
   if (kind == 1) return (qp - qm) / (2.0 * h); /* central, as printed */
-  /* van Albada et al. (1982) smooth limited average */
   double a = q0 - qm, b = qp - q0;
-  return ((b * b + OR_VA_EPS2) * a + (a * a + OR_VA_EPS2) * b) / ((a * a + b * b + 2.0 * OR_VA_EPS2) * h);
+  return va_slope(a, b, h);
+}
+
+/* The same slopes on a non-uniform grid: the cell of width h lies at centre distances hm and
+ * hp from its lower and upper neighbours.  Central: (qp - qm) / (hm + hp); van Albada: the
+ * same average of the one-sided differences scaled to the cell's width, a = (q0 - qm) h / hm,
+ * b = (qp - q0) h / hp (on a uniform grid hm = hp = h and both reduce to the slopes above). */
+static double slope_nu(int kind, double qm, double q0, double qp, double h, double hm, double hp) {
+  if (kind == 1) return (qp - qm) / (hm + hp);
+  return va_slope((q0 - qm) * (h / hm), (qp - q0) * (h / hp), h);
 }
 
 /* the slope of one coefficient from its three cell values along an axis (kind 1 central, */
@@ -483,13 +513,16 @@ static void face_state(const or_solver *S, const or_level *L, int i, int j, int 
   if (pos == 0 || pos == len - 1) return; /* wall-adjacent: zero slope */
   int cm = ax == 0 ? c - 1 : c - L->nx;
   int cp = ax == 0 ? c + 1 : c + L->nx;
-  double h = ax == 0 ? L->dx : L->dy;
+  const double *hs = ax == 0 ? L->hx : L->hy;
+  double h = hs[pos], hm = 0.5 * (hs[pos - 1] + h), hp = 0.5 * (h + hs[pos + 1]);
   for (int q = 0; q < 4; ++q) {
-    double g = slope_of(S->c.slope, L->P[4 * cm + q], L->P[4 * c + q], L->P[4 * cp + q], h);
+    double g = L->uniform ? slope_of(S->c.slope, L->P[4 * cm + q], L->P[4 * c + q], L->P[4 * cp + q], h)
+                          : slope_nu(S->c.slope, L->P[4 * cm + q], L->P[4 * c + q], L->P[4 * cp + q], h, hm, hp);
     p[q] = p[q] + sd * (0.5 * h) * g;
   }
   for (int o = 0; o < n; ++o) {
-    double g = slope_of(S->c.slope, L->F[(size_t)cm * n + o], L->F[(size_t)c * n + o], L->F[(size_t)cp * n + o], h);
+    double qm = L->F[(size_t)cm * n + o], q0 = L->F[(size_t)c * n + o], qp = L->F[(size_t)cp * n + o];
+    double g = L->uniform ? slope_of(S->c.slope, qm, q0, qp, h) : slope_nu(S->c.slope, qm, q0, qp, h, hm, hp);
     f[o] = f[o] + sd * (0.5 * h) * g;
   }
 }
@@ -722,7 +755,7 @@ static void cell_R(const or_solver *S, const or_level *L, int i, int j, double *
     or_hll_flux(M, S->C, 1, pc, pm, fm, pp, fp, FS);
   }
   or_collision(M, cf->model, cf->Kn, cf->Pr, cf->omega, cf->beta, pc, fc, Q);
-  for (int o = 0; o < n; ++o) R[o] = -(FE[o] - FW[o]) / L->dx - (FN[o] - FS[o]) / L->dy + Q[o];
+  for (int o = 0; o < n; ++o) R[o] = -(FE[o] - FW[o]) / L->hx[i] - (FN[o] - FS[o]) / L->hy[j] + Q[o];
 }
 
 /* r of level L in the basis pc (zero when the level has no r) */
@@ -773,7 +806,7 @@ static int regrad(const or_solver *S, const double *p, const double *g, double *
 static double local_dt(const or_solver *S, const or_level *L, int c) {
   const double *pc = L->P + 4 * c, *fc = L->F + (size_t)c * S->n;
   double sq = sqrt(pc[3]);
-  double dt = S->c.cfl / ((fabs(pc[0]) + S->C * sq) / L->dx + (fabs(pc[1]) + S->C * sq) / L->dy);
+  double dt = S->c.cfl / ((fabs(pc[0]) + S->C * sq) / L->hx[c % L->nx] + (fabs(pc[1]) + S->C * sq) / L->hy[c / L->nx]);
   if (S->c.dtnu > 0.0) {
     double nu = S->c.beta * sqrt(M_PI / 2.0) * fc[0] * pow(pc[3], 1.0 - S->c.omega) / S->c.Kn;
     dt = fmin(dt, S->c.dtnu / nu);
@@ -920,7 +953,7 @@ double or_residual(const or_solver *S, int l, double *Rout) {
       double Rc[OR_MAXN];
       or_cell_residual(S, l, c % L->nx, c / L->nx, Rc);
       if (Rout) memcpy(Rout + (size_t)c * S->n, Rc, S->n * sizeof(double));
-      term[c] = local_norm2(S, L->P + 4 * c, Rc) * L->dx * L->dy;
+      term[c] = local_norm2(S, L->P + 4 * c, Rc) * L->hx[c % L->nx] * L->hy[c / L->nx];
     }
     for (int c = 0; c < nc; ++c) acc += term[c];
     free(term);
@@ -931,7 +964,7 @@ double or_residual(const or_solver *S, int l, double *Rout) {
       int c = j * L->nx + i;
       or_cell_residual(S, l, i, j, R);
       if (Rout) memcpy(Rout + (size_t)c * S->n, R, S->n * sizeof(double));
-      acc += local_norm2(S, L->P + 4 * c, R) * L->dx * L->dy;
+      acc += local_norm2(S, L->P + 4 * c, R) * L->hx[i] * L->hy[j];
     }
   return sqrt(acc / (S->c.lx * S->c.ly));
 }
@@ -955,17 +988,23 @@ static void restrict_level(or_solver *S, int lf) {
       int C = J * Lc->nx + I;
       int fi[4] = {(2 * J) * Lf->nx + 2 * I, (2 * J) * Lf->nx + 2 * I + 1, (2 * J + 1) * Lf->nx + 2 * I,
                    (2 * J + 1) * Lf->nx + 2 * I + 1};
+      /* area weights of the children (equal areas: the plain mean, as 1 each and 1/4 at the end) */
+      double wq[4];
+      for (int q = 0; q < 4; ++q)
+        wq[q] = Lf->uniform ? 1.0
+                            : Lf->hx[fi[q] % Lf->nx] * Lf->hy[fi[q] / Lf->nx] / (Lc->hx[I] * Lc->hy[J]);
+      const double mean = Lf->uniform ? 0.25 : 1.0;
       double rho = 0.0, mom[3] = {0, 0, 0}, en = 0.0;
       for (int q = 0; q < 4; ++q) {
         const double *p = Lf->P + 4 * fi[q];
-        double r = Lf->F[(size_t)fi[q] * n];
+        double r = wq[q] * Lf->F[(size_t)fi[q] * n];
         rho += r;
         for (int d = 0; d < 3; ++d) mom[d] += r * p[d];
         en += r * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) + 3.0 * r * p[3];
       }
-      rho *= 0.25;
-      for (int d = 0; d < 3; ++d) mom[d] *= 0.25;
-      en *= 0.25;
+      rho *= mean;
+      for (int d = 0; d < 3; ++d) mom[d] *= mean;
+      en *= mean;
       double pH[4];
       for (int d = 0; d < 3; ++d) pH[d] = mom[d] / rho;
       pH[3] = (en - rho * (pH[0] * pH[0] + pH[1] * pH[1] + pH[2] * pH[2])) / (3.0 * rho);
@@ -978,13 +1017,13 @@ static void restrict_level(or_solver *S, int lf) {
         or_transform(S->c.M, Lf->P + 4 * fi[q], pH, Lf->F + (size_t)fi[q] * n, tf);
         or_transform(S->c.M, Lf->P + 4 * fi[q], pH, Lf->D + (size_t)fi[q] * n, tr);
         for (int o = 0; o < n; ++o) {
-          fH[o] += tf[o];
-          RH[o] += tr[o];
+          fH[o] += wq[q] * tf[o];
+          RH[o] += wq[q] * tr[o];
         }
       }
       for (int o = 0; o < n; ++o) {
-        fH[o] *= 0.25;
-        RH[o] *= 0.25;
+        fH[o] *= mean;
+        RH[o] *= mean;
       }
       /* f_H is in Grad form up to round-off; make it exact */
       fH[idx3(b, 1, 0, 0)] = 0.0;

@@ -26,6 +26,15 @@ def oracle_config(prob):
     c.order, c.slope, c.cfl = prob.order, prob.slope, prob.cfl
     c.s1, c.s2, c.s3, c.gamma = prob.s1, prob.s2, prob.s3, prob.gamma
     c.dtnu = prob.dtnu
+    if getattr(prob, "hx", None) is not None:
+        import ctypes
+
+        import numpy as np
+
+        c._hx = np.ascontiguousarray(prob.hx, dtype=np.float64)  # kept alive with the struct
+        c._hy = np.ascontiguousarray(prob.hy, dtype=np.float64)
+        c.hx = c._hx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.hy = c._hy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     for w in range(4):
         for d in range(3):
             c.wall_u[w][d] = prob.walls[w].u[d]

@@ -61,6 +61,8 @@ class Problem:
     s3: int = 4
     gamma: int = 1
     dtnu: float = 0.0  # > 0: local time step capped at dtnu / nu
+    hx: tuple = None   # widths of the finest level's columns (None: uniform lx / nx)
+    hy: tuple = None   # widths of the finest level's rows (None: uniform ly / ny)
 
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
@@ -102,6 +104,23 @@ def config_c2() -> Problem:
 
 def config_c3() -> Problem:
     return heated_cavity(512, 8, 0.05, theta_bottom=2.0, order=2, slope=2, levels=7, model=SHAKHOV)
+
+
+def stretched_widths(n, length=1.0, ratio=1.5, pairs=True):
+    """Cell widths of a grid refined towards both walls: a geometric progression of `ratio`
+    between the wall cells and the middle ones, scaled to sum to `length`.  With pairs, the
+    widths come in equal pairs (2k, 2k + 1) on the finest level, so every coarser level of the
+    multigrid hierarchy is stretched the same way."""
+    import numpy as np
+
+    half = n // 2
+    g = ratio ** (1.0 / max(half - 1, 1))
+    w = np.array([g ** min(k, n - 1 - k) for k in range(n)], dtype=np.float64)
+    if pairs:
+        w = np.repeat(w.reshape(-1, 2).mean(1), 2) if n % 2 == 0 else w
+    w *= length / w.sum()
+    w[-1] = length - w[:-1].sum()
+    return tuple(float(x) for x in w)
 
 
 def maxwellian_state(ny, nx, M, rho=1.0, theta=1.0):

@@ -56,10 +56,10 @@ MUTANTS = [
      "Lc->rF[q] = Lc->D[q] + Lc->rF[q];", "Lc->rF[q] = Lc->D[q] - Lc->rF[q];",
      [pins.check_fas_restriction_and_coarse_rhs]),
     ("state restricted in place of the defect",
-     "RH[o] += tr[o];", "RH[o] += tf[o];",
+     "RH[o] += wq[q] * tr[o];", "RH[o] += wq[q] * tf[o];",
      [pins.check_fas_restriction_and_coarse_rhs, pins.check_fas_leaves_a_solved_fine_state_unchanged]),
     ("restricted defect summed, not averaged",
-     "RH[o] *= 0.25;", "RH[o] *= 1.0;",
+     "RH[o] *= mean;", "RH[o] *= 1.0;",
      [pins.check_fas_restriction_and_coarse_rhs]),
     ("coarse temperature from the energy with a wrong factor",
      "pH[3] = (en - rho * (pH[0] * pH[0] + pH[1] * pH[1] + pH[2] * pH[2])) / (3.0 * rho);",
