@@ -226,6 +226,32 @@ nrmg_status nrmg_mass_correct(nrmg_ctx *ctx);
 nrmg_status nrmg_set_grid(nrmg_ctx *ctx, int ctas_per_sm);
 int nrmg_grid_limit(const nrmg_ctx *ctx);
 
+/* Two-CTA clusters for the FP64 sweeps of small levels (the paper has no counterpart: it is a
+ * schedule of the same Algorithm 1).  A level whose wavefront is shorter than the GPU is wide
+ * leaves most SMs idle while one SM's FP64 pipe bounds each cell update; levels with at most
+ * max_cells cells (0: none; default 16384, i.e. up to 128 x 128) then split every cell update over a cluster of two
+ * CTAs on two SMs: one takes the x faces, the other the y faces, r, the collision and the
+ * projection back to Grad form, the halves meeting in distributed shared memory (one
+ * cluster CTA per SM on levels of at most 4096 cells, two per SM above).  The serial
+ * order, and so the result up to rounding, is unchanged.  nrmg_cluster_capacity: clusters that
+ * fit on the device at once (0: cluster launch unavailable, the setting is then ignored). */
+nrmg_status nrmg_set_cluster(nrmg_ctx *ctx, int max_cells);
+
+/* Non-uniform grid (Sec. 2.4: the local time step of eq. local-CFL serves non-uniform grids):
+ * host_hx[nx] and host_hy[ny] are the widths of the finest level's columns and rows, positive
+ * and adding up to lx and ly (to 1e-12); a coarse cell merges two columns and two rows of the
+ * next finer level, whose widths add.  Each cell's flux differences are divided by its own
+ * widths, its time step takes them, the second-order slopes use the distances between cell
+ * centres (central: (q+ - q-) / (hm + hp); van Albada: the average of the one-sided
+ * differences scaled to the cell's width, (q0 - q-) h / hm and (q+ - q0) h / hp), the norm of
+ * eq. relative-residual and the mass weigh each cell by its area, and the restriction
+ * averages the four children with their areas.  Call after nrmg_create and before any state
+ * or right-hand side: every level returns to the global Maxwellian and the reference mass and
+ * residual are reset (a batch takes the spacing its contexts have when it is created).
+ * Synchronizes.  Errors: NRMG_ERR_ARG (a width <= 0 or not finite, sums off lx or ly). */
+nrmg_status nrmg_set_spacing(nrmg_ctx *ctx, const double *host_hx, const double *host_hy);
+int nrmg_cluster_capacity(const nrmg_ctx *ctx);
+
 /* Fix the reference of the following cycles: the total mass the correction restores
  * (mass > 0; 0 keeps the current one) and the norm the relative residual divides by
  * (res0 > 0; 0 keeps the current one).  While a residual reference is fixed, nrmg_solve and

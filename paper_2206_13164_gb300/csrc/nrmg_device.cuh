@@ -279,6 +279,23 @@ __device__ inline double half_slope(int slope, double qm, double q0, double qp) 
   return 0.5 * ((a + b) * fma(a, b, VA_EPS2)) * rcp_nr(fma(a, a, fma(b, b, 2.0 * VA_EPS2)));
 }
 
+// The same on a non-uniform grid, with the factors of the cell's column or row: the central
+// slope times h/2 is (qp - qm) ch; the van Albada average takes the one-sided differences
+// scaled to the cell's width, a = (q0 - qm) rm, b = (qp - q0) rp.
+__device__ inline double half_slope_nu(int slope, double qm, double q0, double qp, double rm, double rp,
+                                       double ch) {
+  if (slope == 1) return (qp - qm) * ch;
+  double a = (q0 - qm) * rm, b = (qp - q0) * rp;
+  return 0.5 * ((a + b) * fma(a, b, VA_EPS2)) * rcp_nr(fma(a, a, fma(b, b, 2.0 * VA_EPS2)));
+}
+
+// inverse widths of column i and row j, area of cell (i, j)
+__device__ inline double inv_hx(const LevelDev &L, int i) { return L.uniform ? L.idx : L.ihx[i]; }
+__device__ inline double inv_hy(const LevelDev &L, int j) { return L.uniform ? L.idy : L.ihy[j]; }
+__device__ inline double cell_area(const LevelDev &L, int i, int j) {
+  return L.uniform ? L.dx * L.dy : L.hx[i] * L.hy[j];
+}
+
 // stencil slots: 0 C, 1 E, 2 W, 3 N, 4 S, 5 EE, 6 WW, 7 NN, 8 SS
 static __constant__ int c_nb_di[9] = {0, 1, -1, 0, 0, 2, -2, 0, 0};
 static __constant__ int c_nb_dj[9] = {0, 0, 0, 1, -1, 0, 0, 2, -2};

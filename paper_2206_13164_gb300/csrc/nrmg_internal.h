@@ -33,6 +33,13 @@ struct LevelDev {
   // frozen per-cell coefficients (u1, u2, u3, theta, dt, nu, 0, 0)
   float *e32, *d32, *aux32;
   float *s32;  // FP32 copy of the state's coefficients: the frozen limiter weights of the correction
+  // Non-uniform grid (nrmg_set_spacing; uniform = 1 leaves these NULL and uses dx, dy): widths
+  // hx[nx], hy[ny] and their inverses, and per column (row) the factors of the second-order
+  // reconstruction: rm = h / hm, rp = h / hp (h the cell's width, hm, hp the distances to the
+  // neighbouring centres) and ch = h / (2 (hm + hp))
+  int uniform;
+  const double *hx, *hy, *ihx, *ihy;
+  const double *rmx, *rpx, *chx, *rmy, *rpy, *chy;
 };
 
 // Everything a kernel needs besides the level: scheme constants and
@@ -84,6 +91,14 @@ size_t cell_smem_bytes(int M, int NP);
 // FS^steps on level L.  queue (may be NULL): the order in which the persistent CTAs take the
 // steps*4*ncell items, each item (s*4 + k)*ncell + c; NULL = sweep by sweep in anti-diagonal order.
 cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, const int *queue, int grid, cudaStream_t st);
+// The same sweeps with each cell update split over a cluster of two CTAs on two SMs (x faces on
+// one, y faces, collision and projection on the other); nclusters persistent clusters, per_sm
+// (1 or 2) CTAs per SM.
+cudaError_t launch_fs_cluster(const Consts &K, const LevelDev &L, int steps, const int *queue, int nclusters,
+                              int per_sm, cudaStream_t st);
+// Clusters of the two-CTA sweep that fit on the device at once with per_sm CTAs per SM (0:
+// cluster launch unavailable).
+int cluster_capacity(const Consts &K, int per_sm);
 // FS sweeps of several problems in one persistent launch (items: problem, level-queue item).
 cudaError_t launch_fs_batch(const BatchDesc *desc, const int2 *items, long long total, int *counter,
                             const Consts &K0, int grid, cudaStream_t st);

@@ -76,7 +76,17 @@ __device__ inline void es_equilibrium(int N, int NE, const uint16_t *eidx, const
 // state (E, W, N, S), or 2f = the cell re-expanded in the wall basis when face f is a wall;
 // slot 8 = r.
 // kES: the ES-BGK instantiation (model 2); the other models' instantiation carries no ES code.
-template <bool kCoherent, bool kPreloaded = false, bool kES = false, typename Emit>
+// kPart: 0 the whole residual; 1 only the x faces (E, W), emitting -(F_E - F_W)/dx; 2 the y
+// faces (N, S), the collision and r, emitting -(F_N - F_S)/dy + Q - r (the two halves of one
+// cell update that a cluster of two CTAs computes side by side).
+__host__ __device__ constexpr bool part_has_face(int part, int f) { return part == 0 || (part == 1) == (f < 2); }
+// slope items of a part: 0 C along x, 1 C along y, 2 E, 3 W, 4 N, 5 S
+__host__ __device__ constexpr int part_items(int part) { return part == 0 ? 6 : 3; }
+__host__ __device__ constexpr int part_item(int part, int k) {
+  return part == 0 ? k : (part == 1 ? (k == 0 ? 0 : k + 1) : (k == 0 ? 1 : k + 3));
+}
+
+template <bool kCoherent, bool kPreloaded = false, bool kES = false, int kPart = 0, typename Emit>
 __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, int i, int j, Emit emit) {
   const int N = K.N, NP = K.NP, tid = threadIdx.x;
   const int c = j * L.nx + i;
@@ -116,7 +126,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     }
   }
   if (!kPreloaded && tid < 4) s.iarr[I_WALL + tid] = s.iarr[I_EX + c_face_nb[tid]] ? 0 : 1;
-  if (L.has_r) {
+  if (L.has_r && kPart != 1) {
     for (int e = tid; e < 4 + K.NE; e += kThreads) {
       if (e < 4) {
         s.vsrc[8 * 4 + e] = L.rP[(size_t)c * 4 + e];
@@ -135,13 +145,26 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   const int NE = K.NE;
   // one slope item element: writes the face state(s) it feeds
   auto face_item = [&](int q) {
-    int it = q / (4 + NE), e = q - it * (4 + NE);
+    const int kk = q / (4 + NE);
+    int it = part_item(kPart, kk), e = q - kk * (4 + NE);
     if (e >= 4) e = 4 + s.eidx[e - 4];
     int X = c_it_x[it], Xm = c_it_m[it], Xp = c_it_p[it];
     if (!s.iarr[I_EX + X]) return;
     bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + Xm] && s.iarr[I_EX + Xp];
     double q0 = stencil(s, X, NP)[e];
-    double hs = on ? half_slope(K.slope, stencil(s, Xm, NP)[e], q0, stencil(s, Xp, NP)[e]) : 0.0;
+    double hs = 0.0;
+    if (on) {
+      const double qm = stencil(s, Xm, NP)[e], qp = stencil(s, Xp, NP)[e];
+      if (L.uniform) {
+        hs = half_slope(K.slope, qm, q0, qp);
+      } else if (it == 1 || it >= 4) {  // along y: the row of the item's cell
+        const int r = j + c_nb_dj[X];
+        hs = half_slope_nu(K.slope, qm, q0, qp, L.rmy[r], L.rpy[r], L.chy[r]);
+      } else {
+        const int col = i + c_nb_di[X];
+        hs = half_slope_nu(K.slope, qm, q0, qp, L.rmx[col], L.rpx[col], L.chx[col]);
+      }
+    }
     int v0, v1 = -1;
     double x0, x1 = 0.0;
     switch (it) {
@@ -167,7 +190,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     }
   };
   {
-    const int tot = 6 * (4 + NE);
+    const int tot = part_items(kPart) * (4 + NE);
     for (int q = tid; q < tot; q += 2 * kThreads) {
       face_item(q);
       if (q + kThreads < tot) face_item(q + kThreads);
@@ -187,10 +210,11 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   if (tid == 0) {
     int na = 0;
     for (int f = 0; f < 4; ++f) {
+      if (!part_has_face(kPart, f)) continue;
       s.iarr[I_ACT + na++] = 2 * f;
       if (!s.iarr[I_WALL + f]) s.iarr[I_ACT + na++] = 2 * f + 1;
     }
-    if (L.has_r) s.iarr[I_ACT + na++] = 8;
+    if (L.has_r && kPart != 1) s.iarr[I_ACT + na++] = 8;
     s.iarr[I_NACT] = na;
   }
   if (tid == 32) {
@@ -200,7 +224,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     const double nu = K.nu0 * rho * tpc;
     s.sc[S_NU] = nu;
     double sq = sqrt(th);
-    double dt = K.cfl / ((fabs(pc[0]) + K.C * sq) * L.idx + (fabs(pc[1]) + K.C * sq) * L.idy);
+    double dt = K.cfl / ((fabs(pc[0]) + K.C * sq) * inv_hx(L, i) + (fabs(pc[1]) + K.C * sq) * inv_hy(L, j));
     if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / nu);
     s.sc[S_DT] = dt;
   }
@@ -224,7 +248,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   __syncthreads();
   // ---- HLL weights per interior face: F = w1 Xi a- + w2 Xi a+ + w3 (a+ - a-)
   // (on warp 1, in parallel with warp 0's coefficient recurrences)
-  if (tid >= 32 && tid < 36 && !s.iarr[I_WALL + tid - 32]) {
+  if (tid >= 32 && tid < 36 && !s.iarr[I_WALL + tid - 32] && part_has_face(kPart, tid - 32)) {
     const int f = tid - 32, ax = f >> 1;
     const double *pm = s.vsrc + (2 * f) * 4, *pp = s.vsrc + (2 * f + 1) * 4;
     double sL = fmin(pm[ax] - K.C * sqrt(pm[3]), pp[ax] - K.C * sqrt(pp[3]));
@@ -247,7 +271,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   // ---- batch A: face states -> cell basis, cell -> wall bases, r -> cell basis (result in VB)
   transform_batch(K, s, s.VA, s.VB);
   // ---- wall fluxes (half-range kinetic flux in the wall basis)
-  if (tid < 4 && s.iarr[I_WALL + tid]) {
+  if (tid < 4 && s.iarr[I_WALL + tid] && part_has_face(kPart, tid)) {
     int w = c_face_wall[tid], ax = c_wall_axis[w];
     const double *a = s.VB + (2 * tid) * NP;
     const double *wr = K.wallRho + w * (K.M + 1);
@@ -259,7 +283,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   {
     int nw = 0, wf[4];
     for (int f = 0; f < 4; ++f)
-      if (s.iarr[I_WALL + f]) wf[nw++] = f;
+      if (s.iarr[I_WALL + f] && part_has_face(kPart, f)) wf[nw++] = f;
     for (int q = tid; q < nw * NE; q += kThreads) {
       int k = q / NE, r = q - k * NE;
       int f = wf[k], w = c_face_wall[f], ax = c_wall_axis[w];
@@ -280,7 +304,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
       for (int k = 0; k < nw; ++k) s.iarr[I_ACT + na++] = 2 * wf[k];
       s.iarr[I_NACT] = na;
     }
-    if (tid < 4 && s.iarr[I_WALL + tid]) {
+    if (tid < 4 && s.iarr[I_WALL + tid] && part_has_face(kPart, tid)) {
       int w = c_face_wall[tid];
       double *src = s.vsrc + (2 * tid) * 4, *dst = s.vdst + (2 * tid) * 4;
       for (int e = 0; e < 4; ++e) {
@@ -304,6 +328,7 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     double d[2] = {0.0, 0.0}, ee[2] = {0.0, 0.0};
 #pragma unroll
     for (int fc = 0; fc < 4; ++fc) {
+      if (!part_has_face(kPart, fc)) continue;
       int ax = fc >> 1;
       double sg = (fc & 1) ? -1.0 : 1.0;
       if (s.iarr[I_WALL + fc]) {
@@ -320,16 +345,21 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
     eX[o] = ee[0];
     eY[o] = ee[1];
   }
-  if (kES) es_equilibrium(N, NE, s.eidx, s.tal, s.sc, pc[4], s.VA + 5 * NP);
+  if (kES && kPart != 1) es_equilibrium(N, NE, s.eidx, s.tal, s.sc, pc[4], s.VA + 5 * NP);
   __syncthreads();
   // ---- R = -(F_E - F_W)/dx - (F_N - F_S)/dy + Q
   const double *f = pc + 4;
   const double nu = s.sc[S_NU];
+  const double idx_c = inv_hx(L, i), idy_c = inv_hy(L, j);
   for (int q = tid; q < NE; q += kThreads) {
     const int o = s.eidx[q];
     double xi[2];
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
+      if ((kPart == 1 && ax == 1) || (kPart == 2 && ax == 0)) {
+        xi[ax] = 0.0;
+        continue;
+      }
       const double *dd = ax == 0 ? dX : dY;
       uint16_t pr = s.tprev[ax * N + o], nx = s.tnext[ax * N + o];
       double v = pc[ax] * dd[o];
@@ -347,7 +377,12 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
       fE = s.VA[5 * NP + o];
     }
     double Q = nu * (fE - f[o]);
-    double R = fma(-(xi[0] + eX[o]), L.idx, fma(-(xi[1] + eY[o]), L.idy, Q));
+    if (kPart == 1) {  // the x half: -(F_E - F_W)/dx only
+      emit(o, -(xi[0] + eX[o]) * idx_c);
+      continue;
+    }
+    double R = kPart == 0 ? fma(-(xi[0] + eX[o]), idx_c, fma(-(xi[1] + eY[o]), idy_c, Q))
+                          : fma(-(xi[1] + eY[o]), idy_c, Q);
     double r = L.has_r ? s.VB[8 * NP + o] : 0.0;
     emit(o, R - r);
   }
@@ -405,8 +440,17 @@ __device__ inline bool regrad(const Consts &K, Sm &s, const double *pc, int v, b
 // One sweep item: update cell c (i,j) of sweep k to version v once the cross stencil holds
 // the versions of the serial order (the newest for a neighbour that sweep Dk visits earlier,
 // the previous one otherwise), then publish v.  Returns false when the launch must stop.
-template <bool kES>
-__device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c, int k, int v) {
+// stencil slots of a part: all nine, or the cell and its neighbours along x (E, W, EE, WW) or
+// along y (N, S, NN, SS)
+__host__ __device__ constexpr bool part_has_slot(int part, int sl) {
+  return part == 0 || sl == 0 || (part == 1) == (sl == 1 || sl == 2 || sl == 5 || sl == 6);
+}
+
+// Dependency waits and stencil loads of one sweep item (the slots of part kPart; the existence
+// and wall flags of all nine slots are set either way).  Returns after the CTA barrier; a wait
+// that gave up sets iarr[I_ABW].
+template <int kPart>
+__device__ inline void fs_wait_load(const Consts &K, const LevelDev &L, Sm &s, int c, int k, int v) {
   const int tid = threadIdx.x, NP = K.NP, NE = K.NE;
   const int i = c % L.nx, j = c / L.nx;
   // ---- per stencil slot (warp w takes slot w, warp 0 also slot 8): lane 0 waits until the
@@ -426,7 +470,7 @@ __device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c,
       if (lane == 0) {
         s.iarr[I_EX + sl] = in ? 1 : 0;
         if (sl >= 1 && sl <= 4) s.iarr[I_WALL + sl - 1] = in ? 0 : 1;  // face f = slot f + 1
-        if (in) {
+        if (in && part_has_slot(kPart, sl)) {
           const bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
           const int need = (sl != 0 && before) ? v : v - 1;
           const int *flag = L.ver + (size_t)jj * L.nx + ii;
@@ -477,6 +521,13 @@ __device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c,
     }
   }
   __syncthreads();
+}
+
+template <bool kES>
+__device__ inline bool fs_item(const Consts &K, const LevelDev &L, Sm &s, int c, int k, int v) {
+  const int tid = threadIdx.x, NP = K.NP;
+  const int i = c % L.nx, j = c / L.nx;
+  fs_wait_load<0>(K, L, s, c, k, v);
   if (s.iarr[I_ABW]) return false;
   // ---- R_ij(f) - r_ij, then f + dt (R - r) into VA slot 4, back to Grad form
   cell_residual<true, true, kES>(K, L, s, i, j,
@@ -532,6 +583,189 @@ __global__ void __launch_bounds__(kThreads) fs_kernel(Consts K, LevelDev L, int 
     }
     if (!fs_item<kES>(K, L, s, c, k, 4 * st + k + 1)) break;
   }
+}
+
+// ------------------------------------------------------------------ FS^steps on a cluster of two CTAs
+// On levels whose wavefront is shorter than the GPU is wide, one cell update is split over a
+// cluster of two CTAs on two SMs (the FP64 pipe of one SM bounds a single update): CTA 0 takes
+// the x faces (E, W: their face states, basis transforms, HLL or wall fluxes) and produces
+// -(F_E - F_W)/dx; CTA 1 takes the y faces, r and the collision, adds CTA 0's half read from
+// its shared memory (distributed shared memory of the cluster), updates the cell and projects
+// it back to Grad form.  CTA 0 fetches the work items and hands each to CTA 1 through a mailbox
+// in CTA 1's shared memory; with two exchange buffers it starts the next item while CTA 1
+// finishes the current one.  Every wait on the partner is bounded like the dependency waits.
+__device__ inline unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ inline unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ inline unsigned cluster_map(unsigned a, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ inline void st_cluster(unsigned a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ inline void st_release_cluster(unsigned a, int v) {
+  asm volatile("st.release.cluster.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ inline int ld_acquire_cluster(unsigned a) {
+  int v;
+  asm volatile("ld.acquire.cluster.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ inline double ld_cluster_f64(unsigned a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ inline void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// bounded wait until the word at cluster address a holds at least `need`
+__device__ inline bool wait_cluster_word(const Consts &K, unsigned a, int need) {
+  if (ld_acquire_cluster(a) >= need) return true;
+  const unsigned long long t0 = gtimer();
+  while (ld_acquire_cluster(a) < need) {
+    if (ld_volatile(K.abort_flag)) return false;
+    if (gtimer() - t0 > kWaitLimitNs) {
+      raise_status(K, kStTimeout, true);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// exchange area behind the cell working set: x halves [2][NP] doubles, then control words
+// (mailbox items [2], mailbox sequence, x-half sequence, consumed sequence)
+enum { X_MBOX = 0, X_MSEQ = 2, X_FSEQ = 3, X_CSEQ = 4, X_WORDS = 8 };
+__host__ __device__ inline size_t xchg_offset(int M, int N, int NP) { return al16(make_layout(M, N, NP).total); }
+__host__ __device__ inline size_t cluster_smem_bytes(int M, int N, int NP) {
+  return xchg_offset(M, N, NP) + sizeof(double) * 2 * NP + sizeof(int) * X_WORDS;
+}
+// at least this much dynamic shared memory per CTA: with one CTA per SM the two CTAs of a
+// cluster never share an SM (and its FP64 pipe); with two per SM, two clusters share a pair
+constexpr size_t kClusterMinSmem[2] = {120 * 1024, 78 * 1024};
+
+// CTA 0 of a cluster: the x half of the update of cell c, written to this CTA's exchange
+// buffer xh; then tells CTA 1 (x-half sequence n + 1 in its control words).
+template <bool kES>
+__device__ inline bool fs_item_x(const Consts &K, const LevelDev &L, Sm &s, int c, int k, int v, double *xh,
+                                 unsigned peer_ctl, int n) {
+  const int i = c % L.nx, j = c / L.nx;
+  fs_wait_load<1>(K, L, s, c, k, v);
+  if (s.iarr[I_ABW]) return false;
+  cell_residual<true, true, kES, 1>(K, L, s, i, j, [&](int o, double Rx) { xh[o] = Rx; });
+  // the barrier orders every thread's writes of xh before thread 0's release store (cluster
+  // scope), which CTA 1's acquire load synchronizes with
+  __syncthreads();
+  if (threadIdx.x == 0) st_release_cluster(peer_ctl + 4 * X_FSEQ, n + 1);
+  return true;
+}
+
+// CTA 1 of a cluster: the y half, r and the collision; then CTA 0's x half (read from its
+// shared memory at cluster address peer_xh once the x-half sequence reaches n + 1), the update
+// f + dt (R - r), the projection back to Grad form, the cell's write and its release.
+template <bool kES>
+__device__ inline bool fs_item_y(const Consts &K, const LevelDev &L, Sm &s, int c, int k, int v, unsigned peer_xh,
+                                 unsigned my_ctl, unsigned peer_ctl, int n) {
+  const int tid = threadIdx.x, NP = K.NP;
+  const int i = c % L.nx, j = c / L.nx;
+  fs_wait_load<2>(K, L, s, c, k, v);
+  if (s.iarr[I_ABW]) return false;
+  cell_residual<true, true, kES, 2>(K, L, s, i, j, [&](int o, double Ry) { s.VA[4 * NP + o] = Ry; });
+  if (tid == 0 && !wait_cluster_word(K, my_ctl + 4 * X_FSEQ, n + 1)) s.iarr[I_ABW] = 1;
+  __syncthreads();
+  if (s.iarr[I_ABW]) return false;
+  const double dt = s.sc[S_DT];
+  for (int q = tid; q < K.NE; q += kThreads) {
+    const int o = s.eidx[q];
+    const double rx = ld_cluster_f64(peer_xh + 8u * (unsigned)o);
+    s.VA[4 * NP + o] = fma(dt, rx + s.VA[4 * NP + o], s.cst[4 + o]);
+  }
+  __syncthreads();
+  if (tid == 0) st_release_cluster(peer_ctl + 4 * X_CSEQ, n + 1);  // CTA 0 may reuse the buffer
+  double pcell[4];
+  for (int e = 0; e < 4; ++e) pcell[e] = s.cst[e];
+  bool ok = regrad(K, s, pcell, 4, true);
+  double *Fo = L.F + (size_t)c * NP;
+  for (int q = tid; q < K.NE; q += kThreads) {
+    const int o = s.eidx[q];
+    Fo[o] = s.VB[4 * NP + o];
+  }
+  if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+  if (tid == 4) L.tp[c] = s.sc[S_TPN];
+  if (!ok && tid == 0) raise_status(K, kStNonPhysical, true);
+  __syncthreads();
+  if (tid == 0) st_release(L.ver + c, v);
+  return true;
+}
+
+template <bool kES>
+__global__ void __launch_bounds__(kThreads) fs_cluster_kernel(Consts K, LevelDev L, int steps, const int *queue) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Sm s = bind_smem(smem_raw, K.M, K.N, K.NP);
+  load_tables(K, s);
+  const int tid = threadIdx.x, NP = K.NP;
+  const unsigned rank = cluster_rank(), peer = rank ^ 1u;
+  double *xh = (double *)(smem_raw + xchg_offset(K.M, K.N, NP));
+  int *ctl = (int *)(xh + 2 * NP);
+  if (tid < X_WORDS) ctl[tid] = 0;
+  __syncthreads();
+  cluster_sync_all();  // both CTAs' control words are zero before either writes the other's
+  const unsigned my_ctl = cluster_map(smem_addr(ctl), rank), peer_ctl = cluster_map(smem_addr(ctl), peer);
+  const unsigned peer_xh0 = cluster_map(smem_addr(xh), peer);
+  const int ncell = L.ncell;
+  const long long total = (long long)steps * 4 * ncell;
+  for (int n = 0;; ++n) {
+    if (tid == 0) {
+      int it = (int)total;
+      if (rank == 0) {
+        // the exchange buffer of item n was last used by item n - 2: CTA 1 must be done with it
+        if ((n < 2 || wait_cluster_word(K, my_ctl + 4 * X_CSEQ, n - 1)) && !ld_volatile(K.abort_flag))
+          it = atomicAdd(K.queue, 1);
+        if (it > (int)total) it = (int)total;
+        st_cluster(peer_ctl + 4 * (X_MBOX + (n & 1)), it);
+        st_release_cluster(peer_ctl + 4 * X_MSEQ, n + 1);
+      } else if (wait_cluster_word(K, my_ctl + 4 * X_MSEQ, n + 1)) {
+        it = ctl[X_MBOX + (n & 1)];
+      }
+      s.iarr[I_ITEM] = it;
+      s.iarr[I_ABW] = 0;
+    }
+    __syncthreads();
+    const long long item = s.iarr[I_ITEM];
+    if (item >= total) break;
+    int st, k, c;
+    if (queue) {
+      const int qv = queue[item];
+      st = qv / (4 * ncell);
+      k = (qv / ncell) % 4;
+      c = qv % ncell;
+    } else {
+      st = (int)(item / (4LL * ncell));
+      k = (int)((item / ncell) % 4);
+      c = L.order[(size_t)k * ncell + (int)(item % ncell)];
+    }
+    const int v = 4 * st + k + 1;
+    const bool ok = rank == 0 ? fs_item_x<kES>(K, L, s, c, k, v, xh + (n & 1) * NP, peer_ctl, n)
+                              : fs_item_y<kES>(K, L, s, c, k, v, peer_xh0 + 8u * (unsigned)((n & 1) * NP), my_ctl,
+                                               peer_ctl, n);
+    if (!ok) {
+      // leaving early: release the partner from its mailbox wait
+      if (rank == 0 && tid == 0) {
+        st_cluster(peer_ctl + 4 * (X_MBOX + ((n + 1) & 1)), (int)total);
+        st_release_cluster(peer_ctl + 4 * X_MSEQ, n + 2);
+      }
+      break;
+    }
+  }
+  __syncthreads();
+  cluster_sync_all();  // neither CTA leaves while the other may still read its shared memory
 }
 
 // FS sweeps of several problems (same scheme, any M) in one persistent launch.  items[q] =
@@ -607,7 +841,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L
         for (int o = tid; o < K.N; o += kThreads)
           if (s.tal[2 * K.N + o] & 1) out[(size_t)c * out_stride + o] = 0.0;
       double t = block_sum(loc, s.sc + S_RED);
-      if (tid == 0) acc += t * L.dx * L.dy;
+      if (tid == 0) acc += L.uniform ? t * L.dx * L.dy : t * (L.hx[i] * L.hy[j]);
     } else if (mode == kResDefect) {
       cell_residual<false, false, kES>(K, L, s, i, j, [&](int o, double Rr) { L.D[(size_t)c * NP + o] = -Rr; });
     } else {
@@ -643,17 +877,22 @@ __global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev L
     __syncthreads();
     if (tid == 0) {
       // (u_H, theta_H) from conservation of mass, momentum and energy (eq. uH-thetaH-computation)
+      // children's area weights (equal areas: 1 each, then the plain mean)
+      const double mean = Lf.uniform ? 0.25 : 1.0;
+      for (int q = 0; q < 4; ++q)
+        s.sc[S_W + q] = Lf.uniform ? 1.0
+                                   : Lf.hx[fi[q] % Lf.nx] * Lf.hy[fi[q] / Lf.nx] / (Lc.hx[I] * Lc.hy[J]);
       double rho = 0.0, mom[3] = {0.0, 0.0, 0.0}, en = 0.0;
       for (int q = 0; q < 4; ++q) {
         const double *p = s.vsrc + q * 4;
-        double r = s.VA[q * NP];
+        double r = s.sc[S_W + q] * s.VA[q * NP];
         rho += r;
         for (int d = 0; d < 3; ++d) mom[d] += r * p[d];
         en += r * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) + 3.0 * r * p[3];
       }
-      rho *= 0.25;
-      for (int d = 0; d < 3; ++d) mom[d] *= 0.25;
-      en *= 0.25;
+      rho *= mean;
+      for (int d = 0; d < 3; ++d) mom[d] *= mean;
+      en *= mean;
       double *pH = s.sc + S_PH;
       for (int d = 0; d < 3; ++d) pH[d] = mom[d] / rho;
       pH[3] = (en - rho * (pH[0] * pH[0] + pH[1] * pH[1] + pH[2] * pH[2])) / (3.0 * rho);
@@ -673,12 +912,21 @@ __global__ void __launch_bounds__(kThreads) restrict_kernel(Consts K, LevelDev L
     for (int q = tid; q < NE; q += kThreads) {
       const int o = s.eidx[q];
       double a = 0.0, b = 0.0;
-      for (int q = 0; q < 4; ++q) {
-        a += s.VB[q * NP + o];
-        b += s.VB[(4 + q) * NP + o];
+      if (Lf.uniform) {
+        for (int q = 0; q < 4; ++q) {
+          a += s.VB[q * NP + o];
+          b += s.VB[(4 + q) * NP + o];
+        }
+        a *= 0.25;
+        b *= 0.25;
+      } else {
+        for (int q = 0; q < 4; ++q) {
+          a += s.sc[S_W + q] * s.VB[q * NP + o];
+          b += s.sc[S_W + q] * s.VB[(4 + q) * NP + o];
+        }
       }
-      fH[o] = a * 0.25;
-      RH[o] = b * 0.25;
+      fH[o] = a;
+      RH[o] = b;
     }
     __syncthreads();
     if (tid == 0) {
@@ -762,7 +1010,8 @@ __global__ void euler_dt_kernel(Consts K, LevelDev L, double *dt_out) {
   for (int c = threadIdx.x; c < L.ncell; c += kThreads) {
     const double *p = L.P + (size_t)c * 4;
     const double sq = sqrt(p[3]);
-    double dt = K.cfl / ((fabs(p[0]) + K.C * sq) * L.idx + (fabs(p[1]) + K.C * sq) * L.idy);
+    const int ci = c % L.nx, cj = c / L.nx;
+    double dt = K.cfl / ((fabs(p[0]) + K.C * sq) * inv_hx(L, ci) + (fabs(p[1]) + K.C * sq) * inv_hy(L, cj));
     if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / (K.nu0 * L.F[(size_t)c * K.NP] * L.tp[c]));
     m = fmin(m, dt);
   }
@@ -818,7 +1067,7 @@ __global__ void mass_partial_kernel(LevelDev L, int NP, double *partials) {
   __shared__ double red[kThreads / 32];
   double v = 0.0;
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads)
-    v += L.F[(size_t)c * NP];
+    v += L.uniform ? L.F[(size_t)c * NP] : L.F[(size_t)c * NP] * cell_area(L, c % L.nx, c / L.nx);
   double t = block_sum(v, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
@@ -901,6 +1150,8 @@ static void init_attrs() {
   if (done) return;
   cudaFuncSetAttribute(fs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(fs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(fs_cluster_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(fs_cluster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(residual_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(residual_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(restrict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -922,6 +1173,45 @@ cudaError_t launch_fs(const Consts &K, const LevelDev &L, int steps, const int *
   else
     fs_kernel<false><<<grid, kThreads, smem_for(K), st>>>(K, L, steps, queue);
   return cudaGetLastError();
+}
+
+static cudaLaunchConfig_t cluster_config(const Consts &K, int nclusters, int per_sm, cudaStream_t st,
+                                         cudaLaunchAttribute *attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * nclusters, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = std::max(cluster_smem_bytes(K.M, K.N, K.NP), kClusterMinSmem[per_sm > 1 ? 1 : 0]);
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+cudaError_t launch_fs_cluster(const Consts &K, const LevelDev &L, int steps, const int *queue, int nclusters,
+                              int per_sm, cudaStream_t st) {
+  init_attrs();
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config(K, nclusters, per_sm, st, attr);
+  if (K.model == 2) return cudaLaunchKernelEx(&cfg, fs_cluster_kernel<true>, K, L, steps, queue);
+  return cudaLaunchKernelEx(&cfg, fs_cluster_kernel<false>, K, L, steps, queue);
+}
+
+int cluster_capacity(const Consts &K, int per_sm) {
+  init_attrs();
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config(K, 1, per_sm, nullptr, attr);
+  int n = 0;
+  cudaError_t e = K.model == 2 ? cudaOccupancyMaxActiveClusters(&n, fs_cluster_kernel<true>, &cfg)
+                               : cudaOccupancyMaxActiveClusters(&n, fs_cluster_kernel<false>, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 cudaError_t launch_fs_batch(const BatchDesc *desc, const int2 *items, long long total, int *counter,
@@ -986,7 +1276,9 @@ cudaError_t launch_reduce_norm(const double *partials, int n, double scale, doub
 cudaError_t launch_mass(const Consts &K, const LevelDev &L, double *partials, int grid, double *scal, double m0,
                         bool apply, cudaStream_t st) {
   mass_partial_kernel<<<grid, kThreads, 0, st>>>(L, K.NP, partials);
-  mass_total_kernel<<<1, kThreads, 0, st>>>(partials, grid, L.dx * L.dy, m0, scal);
+  // a uniform grid sums rho and scales by the common cell area; otherwise the partials hold
+  // rho times each cell's area
+  mass_total_kernel<<<1, kThreads, 0, st>>>(partials, grid, L.uniform ? L.dx * L.dy : 1.0, m0, scal);
   if (apply) {
     int g2 = (int)(((size_t)L.ncell * K.NP + kThreads - 1) / kThreads);
     if (g2 > 4096) g2 = 4096;

@@ -102,7 +102,7 @@ __global__ void mixed_prep_kernel(Consts K, LevelDev L) {
     const double *p = L.P + (size_t)c * 4;
     const double rho = L.F[(size_t)c * K.NP], th = p[3], sq = sqrt(th);
     const double nu = K.nu0 * rho * L.tp[c];
-    double dt = K.cfl / ((fabs(p[0]) + K.C * sq) * L.idx + (fabs(p[1]) + K.C * sq) * L.idy);
+    double dt = K.cfl / ((fabs(p[0]) + K.C * sq) * inv_hx(L, c % L.nx) + (fabs(p[1]) + K.C * sq) * inv_hy(L, c / L.nx));
     if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / nu);
     float *a = L.aux32 + (size_t)c * 8;
     for (int e = 0; e < 4; ++e) a[e] = (float)p[e];
@@ -235,10 +235,25 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         if (!s.iarr[I_EX + X]) continue;
         bool on = slopes && s.iarr[I_EX + Xm] && s.iarr[I_EX + Xp];
         const float *rx = cstencil(s, X, NP);
+        // reconstruction factors of the item's cell: 1, 1, 1/4 on a uniform grid
+        float rm = 1.0f, rp = 1.0f, ch = 0.25f;
+        if (on && !L.uniform) {
+          if (it == 1 || it >= 4) {
+            const int r = j + c_nb_dj[X];
+            rm = (float)L.rmy[r], rp = (float)L.rpy[r], ch = (float)L.chy[r];
+          } else {
+            const int col = i + c_nb_di[X];
+            rm = (float)L.rmx[col], rp = (float)L.rpx[col], ch = (float)L.chx[col];
+          }
+        }
         float q0, hs = 0.0f;
         if (e < 4) {  // face basis: the reconstructed params of the state
           q0 = rx[e];
-          if (on) hs = half_slope_f(K.slope, cstencil(s, Xm, NP)[e], q0, cstencil(s, Xp, NP)[e]);
+          if (on) {
+            const float qm = cstencil(s, Xm, NP)[e], qp = cstencil(s, Xp, NP)[e];
+            hs = L.uniform ? half_slope_f(K.slope, qm, q0, qp)
+                           : (K.slope == 1 ? (qp - qm) * ch : half_slope_f(K.slope, q0 - (q0 - qm) * rm, q0, q0 + (qp - q0) * rp));
+          }
         } else {      // correction: the limited slope linearized with frozen weights
           e = 4 + s.eidx[e - 4];
           const int o = e - 4;
@@ -246,11 +261,15 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
           if (on) {
             const float em = cstencil(s, Xm, NP)[8 + o], ep = cstencil(s, Xp, NP)[8 + o];
             if (K.slope == 1) {
-              hs = 0.25f * (ep - em);
-            } else {
+              hs = L.uniform ? 0.25f * (ep - em) : (ep - em) * ch;
+            } else if (L.uniform) {
               const float a = ss[X * NP + o] - ss[Xm * NP + o], b = ss[Xp * NP + o] - ss[X * NP + o];
               const float den = fmaf(a, a, fmaf(b, b, 2e-12f));
               hs = __fdividef(0.5f * (fmaf(b, b, 1e-12f) * (q0 - em) + fmaf(a, a, 1e-12f) * (ep - q0)), den);
+            } else {
+              const float a = (ss[X * NP + o] - ss[Xm * NP + o]) * rm, b = (ss[Xp * NP + o] - ss[X * NP + o]) * rp;
+              const float den = fmaf(a, a, fmaf(b, b, 2e-12f));
+              hs = __fdividef(0.5f * (fmaf(b, b, 1e-12f) * (q0 - em) * rm + fmaf(a, a, 1e-12f) * (ep - q0) * rp), den);
             }
           }
         }
@@ -400,7 +419,7 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     __syncthreads();
     // ---- L e - d and the Gauss-Seidel update e <- e + dt (L e - d)
     const float nu = ac[5], dt = ac[4];
-    const float idx = (float)L.idx, idy = (float)L.idy, shk = (float)((1.0 - K.Pr) * 0.2);
+    const float idx = (float)inv_hx(L, i), idy = (float)inv_hy(L, j), shk = (float)((1.0 - K.Pr) * 0.2);
     const float e2m = (ec[K.idx_2e[0]] + ec[K.idx_2e[1]] + ec[K.idx_2e[2]]) * (1.0f / 3.0f);
     // ES-BGK: the degree-2 part of f^E is (1 - 1/Pr) times the trace-free degree-2 part of f
     // exactly; its degree >= 4 part is quadratic in the stress and is left out of the response

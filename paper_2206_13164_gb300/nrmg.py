@@ -86,6 +86,12 @@ def lib():
         L.nrmg_set_grid.argtypes = [c_void_p, c_int]
         L.nrmg_grid_limit.restype = c_int
         L.nrmg_grid_limit.argtypes = [c_void_p]
+        L.nrmg_set_spacing.restype = c_int
+        L.nrmg_set_spacing.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.nrmg_set_cluster.restype = c_int
+        L.nrmg_set_cluster.argtypes = [c_void_p, c_int]
+        L.nrmg_cluster_capacity.restype = c_int
+        L.nrmg_cluster_capacity.argtypes = [c_void_p]
         L.nrmg_mixed_fallback.restype = c_int
         L.nrmg_mixed_fallback.argtypes = [c_void_p]
         L.nrmg_euler.restype = c_int
@@ -212,6 +218,10 @@ def tune_key(device, shapes, opts, model):
     return f"{_device_tag(device)}|{sh}|order{opts.order}:slope{opts.slope}:prec{opts.precision}|model{model}"
 
 
+# levels of at most this many cells sweep on two-CTA clusters unless set_cluster says otherwise
+CLUSTER_CELLS_DEFAULT = 128 * 128
+
+
 class Solver:
     """One cavity problem on the current CUDA device.
 
@@ -249,6 +259,8 @@ class Solver:
                                 ctypes.byref(self.ctx))
         if st != OK:
             raise NrmgError(st, "nrmg_create")
+        self.cluster_cells = CLUSTER_CELLS_DEFAULT  # the library's default (nrmg_set_cluster)
+        self.cluster_times = {}
 
     # -- helpers
     def _check(self, st, where):
@@ -360,12 +372,36 @@ class Solver:
         self._check(self.L.nrmg_set_grid(self.ctx, ctas_per_sm), "nrmg_set_grid")
         self.tuned = ctas_per_sm
 
+    def set_spacing(self, hx, hy):
+        """Non-uniform grid: widths of the finest level's columns (nx) and rows (ny), adding up
+        to lx and ly.  Resets every level to the global Maxwellian."""
+        import numpy as np
+
+        ax = np.ascontiguousarray(hx, dtype=np.float64)
+        ay = np.ascontiguousarray(hy, dtype=np.float64)
+        if ax.shape != (self.nx,) or ay.shape != (self.ny,):
+            raise ValueError(f"expected {self.nx} column widths and {self.ny} row heights")
+        self._check(self.L.nrmg_set_spacing(self.ctx, c_void_p(ax.ctypes.data), c_void_p(ay.ctypes.data)),
+                    "nrmg_set_spacing")
+
+    def set_cluster(self, max_cells: int):
+        """FP64 sweeps of levels with at most max_cells cells split each cell update over a
+        cluster of two CTAs (0: never)."""
+        self._check(self.L.nrmg_set_cluster(self.ctx, int(max_cells)), "nrmg_set_cluster")
+        self.cluster_cells = int(max_cells)
+
+    @property
+    def cluster_capacity(self) -> int:
+        return int(self.L.nrmg_cluster_capacity(self.ctx))
+
     def tune_key(self):
         return tune_key(self.device, [(self.nx, self.ny, self.M, self.levels)], self.opts, self.coll.model)
 
-    def autotune(self, candidates=None, reps=1, cache=None):
+    def autotune(self, candidates=None, reps=1, cache=None, clusters=()):
         """Time `reps` FAS cycles per candidate CTAs/SM of the sweep launches (the cycles advance
         the solution, not its fixed point) and keep the fastest.  Returns {candidate: s/cycle}.
+        clusters: candidate level sizes (cells) up to which the FP64 sweeps use two-CTA
+        clusters, timed after the grid (results in self.cluster_times).
         cache: a JSON file path (True: TUNE_CACHE) keyed by tune_key(); a cached entry is used
         without timing (the returned dict is then the cached timings), a new result is stored."""
         import time
@@ -379,6 +415,7 @@ class Solver:
         limit = int(self.L.nrmg_grid_limit(self.ctx))
         cands = [c for c in (candidates or range(1, limit + 1)) if 1 <= c <= limit]
         times = {}
+        self.cluster_times = {}
         for c in cands:
             self.set_grid(c)
             torch.cuda.synchronize(self.device)
@@ -389,6 +426,17 @@ class Solver:
             times[c] = (time.perf_counter() - t0) / reps
         best = min(times, key=times.get)
         self.set_grid(best)
+        if clusters and self.cluster_capacity > 0:
+            # then the largest level size whose sweeps run on two-CTA clusters
+            for cells in clusters:
+                self.set_cluster(cells)
+                torch.cuda.synchronize(self.device)
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    self.fas_cycle()
+                torch.cuda.synchronize(self.device)
+                self.cluster_times[cells] = (time.perf_counter() - t0) / reps
+            self.set_cluster(min(self.cluster_times, key=self.cluster_times.get))
         if path:
             _tune_store(path, self.tune_key(), best, times)
         return times
@@ -549,12 +597,16 @@ class Batch:
 
 
 def from_problem(prob, **kw) -> Solver:
-    """Build a Solver from any object with the fields of a cavity problem description."""
+    """Build a Solver from any object with the fields of a cavity problem description (a
+    non-uniform grid when it carries column widths hx and row heights hy)."""
     walls = [(tuple(w.u), w.theta, w.chi) for w in prob.walls]
-    return Solver(prob.nx, prob.ny, prob.M, prob.Kn, walls, levels=prob.levels, lx=prob.lx, ly=prob.ly,
-                  model=prob.model, Pr=prob.Pr, omega=prob.omega, beta=prob.beta, order=prob.order,
-                  slope=prob.slope, cfl=prob.cfl, s1=prob.s1, s2=prob.s2, s3=prob.s3, gamma=prob.gamma,
-                  dtnu=getattr(prob, "dtnu", 0.0), **kw)
+    S = Solver(prob.nx, prob.ny, prob.M, prob.Kn, walls, levels=prob.levels, lx=prob.lx, ly=prob.ly,
+               model=prob.model, Pr=prob.Pr, omega=prob.omega, beta=prob.beta, order=prob.order,
+               slope=prob.slope, cfl=prob.cfl, s1=prob.s1, s2=prob.s2, s3=prob.s3, gamma=prob.gamma,
+               dtnu=getattr(prob, "dtnu", 0.0), **kw)
+    if getattr(prob, "hx", None) is not None:
+        S.set_spacing(prob.hx, prob.hy)
+    return S
 
 
 def residual_noalloc(prob, params, coeffs, want_R=True, stream=None):

@@ -94,6 +94,54 @@ def test_fs_step_parity(name, prob, amp):
     assert_close(N(Fg), Fo, 1e-12, "coeffs")
 
 
+CLUSTER_CASES = ["lid_o1_M3_13x7", "lid_o2va_M6_16", "heat_shak_o2va_M5_16", "lid_M10_o2va_8",
+                 "four_sided_o2va_M5_12", "lid_M16_o2va_6x5", "lid_esbgk_o2va_M8_12x9", "partial_wall_chi"]
+
+
+@pytest.mark.parametrize("name", CLUSTER_CASES)
+def test_fs_parity_on_two_cta_clusters(name):
+    """FS steps with every cell update split over a cluster of two CTAs (x faces on one SM; y
+    faces, r, collision and projection on the other), with a right-hand side, against the
+    oracle: the serial order of Algorithm 1 is kept."""
+    prob, amp = {c[0]: (c[1], c[2]) for c in CASES}[name]
+    rng = np.random.default_rng(105)
+    P, F = random_state(rng, prob.ny, prob.nx, prob.M, amp=amp)
+    rP, rF = random_rhs(rng, prob.ny, prob.nx, prob.M, amp=0.02)
+    G, O = gpu(prob), oracle_solver(prob)
+    assert G.cluster_capacity > 0
+    G.set_cluster(1 << 30)
+    set_both(G, O, 0, P, F)
+    G.set_rhs(0, T(rP), T(rF))
+    O.set_rhs(0, rP, rF)
+    G.smooth(0, 2)
+    O.smooth(0, 2)
+    Pg, Fg = G.get_state(0)
+    Po, Fo = O.get_state(0)
+    assert_close(N(Pg), Po, 1e-12, "params")
+    assert_close(N(Fg), Fo, 1e-12, "coeffs")
+
+
+def test_fas_cycles_on_two_cta_clusters():
+    """Whole V-cycles with the cluster sweeps on the levels up to 16x16 and the one-CTA sweeps
+    above: the oracle's cycles, and the one-CTA schedule's, to rounding."""
+    prob = lid_cavity(32, 5, 0.05, 0.3, order=2, slope=2, levels=3)
+    rng = np.random.default_rng(106)
+    P, F = random_state(rng, 32, 32, 5, amp=0.03)
+    G, H, O = gpu(prob), gpu(prob), oracle_solver(prob)
+    G.set_cluster(16 * 16)
+    G.set_state(T(P), T(F))
+    H.set_state(T(P), T(F))
+    O.set_state(2, P, F)
+    for _ in range(2):
+        rg, rh = G.fas_cycle(), H.fas_cycle()
+        st, ro = O.fas_cycle()
+        assert st == 0 and abs(rg - ro) <= 1e-10 * ro and abs(rg - rh) <= 1e-12 * rh
+    Pg, Fg = G.get_state()
+    Po, Fo = O.get_state(2)
+    assert_close(N(Pg), Po, 1e-11, "params")
+    assert_close(N(Fg), Fo, 1e-11, "coeffs")
+
+
 @pytest.mark.parametrize("name", ["lid_dtnu_M4_12", "heat_shak_o2va_M5_16", "lid_esbgk_o2va_M8_12x9"])
 def test_euler_step_parity(name):
     """Forward Euler (eq. euler-scheme, global step of eq. global-CFL), three steps."""
