@@ -10,7 +10,7 @@ metric: cell-moment updates per second = 4 sweeps x cells x N_M per FS step, sum
 FS steps of every level in the timed cycles (residual evaluations are not counted).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload lid256|lid32|lid64|heat512|batch64|learned512]
+                  [--workload lid256|lid32|lid64|lid128|heat512|batch64|learned512]
 
 The JSON line also reports the same cycle with the mixed-precision smoother (FP32 correction
 sweeps inside FP64 defect correction) and, at N=1, the wall time to relative residual 1e-8 of
@@ -47,6 +47,9 @@ WORKLOADS = {
     "lid64": dict(nx=64, M=10, Kn=0.01, lid=0.5, heat=None, model=0, Pr=2 / 3, order=2, slope=2, levels=4,
                   desc="lid-driven cavity 64x64, M=10 (286 moments), BGK, Kn=0.01, lid 0.5, "
                        "2nd-order van Albada, 4-level FAS V-cycle (2,2,4) (small profiling case)"),
+    "lid128": dict(nx=128, M=10, Kn=0.01, lid=0.5, heat=None, model=0, Pr=2 / 3, order=2, slope=2, levels=5,
+                   desc="lid-driven cavity 128x128, M=10 (286 moments), BGK, Kn=0.01, lid 0.5, "
+                        "2nd-order van Albada, 5-level FAS V-cycle (2,2,4) (profiling case of the one-CTA sweep)"),
     "heat512": dict(nx=512, M=8, Kn=0.05, lid=0.0, heat=2.0, model=1, Pr=2 / 3, order=2, slope=2, levels=7,
                     desc="bottom-heated cavity 512x512, M=8 (165 moments), Shakhov Pr=2/3, Kn=0.05, "
                          "theta_bottom=2, 2nd-order van Albada, 7-level FAS V-cycle (2,2,4)"),
@@ -169,9 +172,9 @@ def nmom(M):
 
 
 # DRAM bytes (read + write) per FS launch, averaged over the 11 FS launches of one V-cycle of
-# the 256x256 M=10 workload, from one ncu capture of the current sweep kernel; no figure for
-# the other workloads
-FS_TRAFFIC_BYTES_PER_LAUNCH = {"lid256": 389.4e6}
+# the 256x256 M=10 workload, from one ncu capture of the current sweep kernels (one-CTA and
+# two-CTA cluster sweeps); no figure for the other workloads
+FS_TRAFFIC_BYTES_PER_LAUNCH = {"lid256": 392.5e6}
 
 LEARNED_KEYS = ("status", "cycles", "final_cycles", "wasted_cycles", "rel_res", "rel_res_after_climb",
                 "coarse_cycles", "t_coarse", "t_climb", "t_final", "t_total", "climb")
@@ -506,7 +509,8 @@ def workload_summary(w, args, dev, steps=3):
     S = make()
     for _ in range(args.warmup):
         S.fas_cycle()
-    tune = S.autotune(candidates=(1, 2, 3), reps=1)
+    tune = S.autotune(candidates=(1, 2, 3), reps=1, clusters=CLUSTER_CANDIDATES)
+    cluster_cells = S.cluster_cells
     S.set_profiling(True)
     S.fs_profile()
     torch.cuda.synchronize(dev)
@@ -528,7 +532,9 @@ def workload_summary(w, args, dev, steps=3):
     peak = fp64_peak(props.multi_processor_count)
     rec = {"workload": w["desc"], "value": cycle_updates(w) * steps / (ms * 1e-3), "unit": "cell-moment updates/s",
            "ms_per_step": ms / steps, "steps": steps, "autotune_ctas_per_sm": grid, "autotune_s_per_cycle": tune,
-           "roofline": {"bound": "alu", "kernel": "fs_kernel (persistent FS sweep, all levels)", "achieved": ach,
+           "two_cta_cluster_sweeps_max_cells": cluster_cells,
+           "roofline": {"bound": "alu", "kernel": "FP64 FS sweeps of all levels (fs_kernel and fs_cluster_kernel)",
+                        "achieved": ach,
                         "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "fs_ms_per_step": fs_ms / steps,
                         "peak_source": "derived FP64 pipe peak"}}
     mixed, mgrid = mixed_cycle_timing(w, make, args, dev, props, 1, lambda: None, steps=steps)
@@ -564,6 +570,11 @@ def extra_workloads(args, dev):
         out[name]["wall_s"] = time.perf_counter() - t0
         torch.cuda.empty_cache()
     return out
+
+
+# level sizes (cells) up to which the FP64 sweeps may run on two-CTA clusters, tried by the
+# autotuner after the grid
+CLUSTER_CANDIDATES = (0, 4096, 16384)
 
 
 def fp64_peak(nsm):
@@ -737,7 +748,7 @@ def main():
     for _ in range(args.warmup):
         S.fas_cycle()
     # sweep grid: persistent CTAs per SM picked by timing one cycle each (untimed warm-up)
-    tune_plain = S.autotune(candidates=(1, 2, 3), reps=1)
+    tune_plain = S.autotune(candidates=(1, 2, 3), reps=1, clusters=CLUSTER_CANDIDATES)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = None
     try:
@@ -815,6 +826,8 @@ def main():
     res_ach = res_fl / (res_ms * 1e-3) / 1e12 if res_ms > 0 else None
     clocks = clk.summary()
     plain_grid = S.tuned
+    plain_cluster = {"max_cells": S.cluster_cells, "capacity": S.cluster_capacity,
+                     "s_per_cycle": {str(k): v for k, v in S.cluster_times.items()}}
     del S
     torch.cuda.empty_cache()
 
@@ -831,8 +844,10 @@ def main():
                        "l2": "inputs larger than L2 (finest-level coefficient array alone is "
                              f"{w['nx'] ** 2 * ((nmom(w['M']) + 3) // 4 * 4) * 8 / 1e6:.0f} MB)",
                        "parallelism": f"replicas x{world}", "rel_residual_after": rel,
-                       "autotune_ctas_per_sm": plain_grid, "autotune_s_per_cycle": tune_plain},
-            "roofline": {"bound": "alu", "kernel": "fs_kernel (persistent FS sweep, all levels)",
+                       "autotune_ctas_per_sm": plain_grid, "autotune_s_per_cycle": tune_plain,
+                       "two_cta_cluster_sweeps": plain_cluster},
+            "roofline": {"bound": "alu", "kernel": "FP64 FS sweeps of all levels (fs_kernel, one CTA per update, "
+                                                  "and fs_cluster_kernel, two-CTA clusters on the small levels)",
                          "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                          "frac": (achieved / peak_nominal) if achieved else None,
                          "traffic": FS_TRAFFIC_BYTES_PER_LAUNCH.get(args.workload),
