@@ -104,7 +104,7 @@ def batch64_measure(args, dev, world=1):
         # one batch of all 64 problems (both M): one persistent launch per stage
         batches = {"all": nrmg.Batch([S for g in groups.values() for _, S in g])}
         t_build = time.perf_counter() - t0
-        tune = {M: B.autotune() for M, B in batches.items()}
+        tune = {M: B.autotune(candidates=(2, 3, 4, 5, 6)) for M, B in batches.items()}
         for _ in range(args.warmup):
             for B in batches.values():
                 B.fas_cycle()
@@ -509,7 +509,7 @@ def workload_summary(w, args, dev, steps=3):
     S = make()
     for _ in range(args.warmup):
         S.fas_cycle()
-    tune = S.autotune(candidates=(1, 2, 3), reps=1, clusters=CLUSTER_CANDIDATES)
+    tune = S.autotune(candidates=(1, 2, 3, 4), reps=1, clusters=CLUSTER_CANDIDATES)
     cluster_cells = S.cluster_cells
     S.set_profiling(True)
     S.fs_profile()
@@ -748,7 +748,7 @@ def main():
     for _ in range(args.warmup):
         S.fas_cycle()
     # sweep grid: persistent CTAs per SM picked by timing one cycle each (untimed warm-up)
-    tune_plain = S.autotune(candidates=(1, 2, 3), reps=1, clusters=CLUSTER_CANDIDATES)
+    tune_plain = S.autotune(candidates=(1, 2, 3, 4), reps=1, clusters=CLUSTER_CANDIDATES)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = None
     try:

@@ -637,3 +637,30 @@ def test_esbgk_iteration_counts_against_table4():
     Kn = 0.1 and M = 5, 10 at Kn = 1, single-level FS and forward Euler within 30% for M = 5."""
     seen = _check_paper_rows([r for r in _paper_rows() if r[0] == "Table4"])
     assert len(seen) >= 9
+
+
+@pytest.mark.parametrize("cluster", [False, True], ids=["one_cta", "two_cta_cluster"])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 5), (5, 1), (2, 2), (3, 7)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_degenerate_grids_on_both_schedules(shape, cluster):
+    """Grids of one row or column, a single cell, and cells with no interior neighbour along an
+    axis (every face a wall, no second-order slope): two FS steps with a right-hand side
+    against the oracle, on the one-CTA and the two-CTA cluster schedules."""
+    nx, ny = shape
+    prob = lid_cavity(nx, 4, 0.1, 0.3, order=2, slope=2).replace(ny=ny)
+    rng = np.random.default_rng(107)
+    P, F = random_state(rng, ny, nx, 4, amp=0.05)
+    rP, rF = random_rhs(rng, ny, nx, 4, amp=0.02)
+    G, O = gpu(prob), oracle_solver(prob)
+    G.set_cluster((1 << 30) if cluster else 0)
+    set_both(G, O, 0, P, F)
+    G.set_rhs(0, T(rP), T(rF))
+    O.set_rhs(0, rP, rF)
+    G.smooth(0, 2)
+    O.smooth(0, 2)
+    Pg, Fg = G.get_state(0)
+    Po, Fo = O.get_state(0)
+    assert_close(N(Pg), Po, 1e-12, "params")
+    assert_close(N(Fg), Fo, 1e-12, "coeffs")
+    Rg, ng = G.residual(0)
+    Ro, no = O.residual(0)
+    assert_close(N(Rg), Ro, 1e-12, "R")
