@@ -1,6 +1,6 @@
 /*
  * nrmg.h -- C ABI of the GB300 (sm_103a) nonlinear-multigrid solver for the
- * regularized Hermite moment discretization of the BGK / Shakhov Boltzmann
+ * regularized Hermite moment discretization of the BGK / Shakhov / ES-BGK Boltzmann
  * equation on a 2D cavity, after Hu & Li, "An efficient nonlinear multigrid
  * solver for the simulation of rarefied gas cavity flow" (arXiv 2206.13164).
  *
@@ -9,8 +9,9 @@
  * Conventions shared by all calls
  * -------------------------------
  * Units are nondimensional (molecular mass 1, velocities in sqrt(R T0)).
- * Grid: nx x ny uniform cells on [0,lx] x [0,ly]; cell (i,j) has index
- *   c = j*nx + i, i along x.  Levels are numbered as in Algorithm 2 of the
+ * Grid: nx x ny cells on [0,lx] x [0,ly], uniform unless nrmg_set_spacing
+ *   gives column widths and row heights; cell (i,j) has index c = j*nx + i,
+ *   i along x.  Levels are numbered as in Algorithm 2 of the
  *   paper: level 0 is the coarsest grid, level levels-1 the finest; level l
  *   has (nx >> (levels-1-l)) x (ny >> (levels-1-l)) cells, formed by merging
  *   2x2 cells (Sec. 3.2.2).

@@ -13,7 +13,10 @@
 // order of the paper would show it: the newest one for a neighbour that sweep Dk visits earlier,
 // the previous one otherwise.  This reproduces the serial sweep exactly while letting
 // consecutive sweeps and steps overlap.  Every wait has a time limit after which the kernel
-// records NRMG_ERR_TIMEOUT and all CTAs leave.
+// records NRMG_ERR_TIMEOUT and all CTAs leave.  On small levels, where the wavefront is shorter
+// than the GPU is wide, each cell update is split over a cluster of two CTAs on two SMs
+// (fs_cluster_kernel).  Non-uniform grids take per-column and per-row widths (LevelDev geometry
+// arrays); uniform grids keep their arithmetic.
 #include "nrmg_device.cuh"
 
 #include <algorithm>
