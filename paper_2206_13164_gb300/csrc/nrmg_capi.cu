@@ -20,7 +20,7 @@ namespace {
 struct Tables {
   int M = 0, N = 0, NE = 0;
   std::vector<int> al;           // [N][3]
-  std::vector<int32_t> i32;      // tslot[3][NE], tshak[N], iq[12], is[6]
+  std::vector<int32_t> i32;      // tslot[3][NE], tshak[N], iq[12], is[6], index lines (tab_i32_size)
   std::vector<uint16_t> u16;     // tmem[3N], tprev[3N], tnext[3N], tal[3N], tdeg[N], eidx[NE]
   std::vector<double> fact;      // [N]
   int idx_axis[2][kMaxM + 1];
@@ -28,6 +28,9 @@ struct Tables {
 };
 
 int nmom(int M) { return (M + 1) * (M + 2) * (M + 3) / 6; }
+
+// entries of tab_i32: tslot[3][NE], tshak[N], iq[12], is[6], then the line tables
+int tab_i32_size(int M) { return 3 * nmom_even(M) + nmom(M) + 18 + nlines_total(M); }
 
 void build_tables(int M, Tables &T) {
   T.M = M;
@@ -55,7 +58,7 @@ void build_tables(int M, Tables &T) {
     if (T.al[3 * o + 2] % 2 == 0) even.push_back(o);
   const int NE = (int)even.size();
   T.NE = NE;
-  T.i32.assign(3 * NE + N + 18, -1);
+  T.i32.assign(tab_i32_size(M), -1);
   T.u16.assign(13 * N + NE, 0xFFFF);
   T.fact.resize(N);
   for (int q = 0; q < NE; ++q) T.u16[13 * N + q] = (uint16_t)even[q];
@@ -92,6 +95,27 @@ void build_tables(int M, Tables &T) {
       T.u16[3 * N + d * N + o] = pm < 0 ? 0xFFFF : (uint16_t)pm;
       T.u16[6 * N + d * N + o] = pp < 0 ? 0xFFFF : (uint16_t)pp;
       T.u16[9 * N + d * N + o] = (uint16_t)T.al[3 * o + d];
+    }
+  }
+  // line tables: per direction, (start in that direction's tmem segment) | (length << 11),
+  // longest first (a warp's lanes then run chains of similar length)
+  {
+    int off = 3 * NE + N + 18;
+    for (int d = 0; d < 3; ++d) {
+      std::vector<std::pair<int, int>> ln;  // (length, start)
+      int pos = 0;
+      for (int o = 0; o < N; ++o) {
+        const int *a = &T.al[3 * o];
+        if (a[d] != 0) continue;
+        const int L = M + 1 - (a[0] + a[1] + a[2]);
+        if (d == 2 || a[2] % 2 == 0) ln.push_back({L, pos});
+        pos += L;
+      }
+      std::stable_sort(ln.begin(), ln.end(), [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+        return x.first > y.first;
+      });
+      for (size_t q = 0; q < ln.size(); ++q) T.i32[off + q] = ln[q].second | (ln[q].first << 11);
+      off += (int)ln.size();
     }
   }
   for (int o = 0; o < N; ++o) {
@@ -379,7 +403,7 @@ std::vector<int> sched_steps(int level, const nrmg_opts *o) {
 void layout(const nrmg_grid *g, int M, const nrmg_opts *opts, Carver &cv, nrmg_ctx *ctx) {
   const int N = nmom(M), NP = pad4(N), NE = nmom_even(M);
   // tables
-  int32_t *ti = cv.take<int32_t>(3 * NE + N + 18);
+  int32_t *ti = cv.take<int32_t>(tab_i32_size(M));
   uint16_t *tu = cv.take<uint16_t>(13 * N + NE);
   double *tf = cv.take<double>(N);
   double *wW = cv.take<double>(4 * (M + 1) * (M + 1));
@@ -429,12 +453,13 @@ void layout(const nrmg_grid *g, int M, const nrmg_opts *opts, Carver &cv, nrmg_c
     L.rpy = L.hy + 3 * L.ny;
     L.chy = L.hy + 4 * L.ny;
     if (opts->precision == 1) {
-      L.e32 = cv.take<float>(nc * NP);
+      L.et = cv.take<unsigned long long>(nc * NP);
       L.d32 = cv.take<float>(nc * NP);
       L.aux32 = cv.take<float>(nc * 8);
       L.s32 = cv.take<float>(nc * NP);
     } else {
-      L.e32 = L.d32 = L.aux32 = L.s32 = nullptr;
+      L.et = nullptr;
+      L.d32 = L.aux32 = L.s32 = nullptr;
     }
     int ns = 0;
     for (int steps : sched_steps(l, opts)) {
@@ -629,8 +654,7 @@ nrmg_status smooth_mixed(nrmg_ctx *ctx, int level, int steps) {
   LevelDev &L = ctx->lev[level];
   nrmg_status s = residual(ctx, level, kResDefect, nullptr, 0, nullptr);
   if (s != NRMG_OK) return s;
-  CK(launch_mixed_prep(ctx->K, L, ctx->stream));
-  CK(cudaMemsetAsync(L.ver, 0, sizeof(int) * L.ncell, ctx->stream));
+  CK(launch_mixed_prep(ctx->K, L, ctx->stream));  // also sets every correction word to version 0
   CK(cudaMemsetAsync(ctx->K.queue, 0, sizeof(int), ctx->stream));
   const int *queue = nullptr;
   for (int q = 0; q < ctx->nsched[level]; ++q)
@@ -770,6 +794,8 @@ nrmg_status nrmg_create(const nrmg_grid *grid, int M, double Kn, const nrmg_wall
     K.NP = ctx->NP;
     K.NE = nmom_even(M);
     K.iq_off = 3 * K.NE + K.N;
+    K.ln_off = K.iq_off + 18;
+    for (int d = 0; d < 3; ++d) K.nl[d] = nlines(M, d);
     K.reach = (opts->order == 2 && opts->slope != 0) ? 2 : 1;
     K.slope = opts->order == 2 ? opts->slope : 0;
     K.model = coll->model;
@@ -1710,7 +1736,7 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
     used += bytes;
     return o;
   };
-  const size_t o_i32 = at((3 * NE + N + 18) * sizeof(int32_t));
+  const size_t o_i32 = at(tab_i32_size(M) * sizeof(int32_t));
   const size_t o_u16 = at((13 * N + NE) * sizeof(uint16_t));
   const size_t o_f64 = at(N * sizeof(double));
   const size_t o_W = at(4 * (M + 1) * (M + 1) * sizeof(double));
@@ -1739,6 +1765,8 @@ extern "C" nrmg_status nrmg_residual_noalloc(const nrmg_grid *grid, int M, doubl
   K.NP = NP;
   K.NE = NE;
   K.iq_off = 3 * NE + N;
+  K.ln_off = K.iq_off + 18;
+  for (int d = 0; d < 3; ++d) K.nl[d] = nlines(M, d);
   K.reach = (opts->order == 2 && opts->slope != 0) ? 2 : 1;
   K.slope = opts->order == 2 ? opts->slope : 0;
   K.model = coll->model;

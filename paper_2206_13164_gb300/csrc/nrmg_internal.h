@@ -29,9 +29,12 @@ struct LevelDev {
   int *ver;         // per-cell update counters of the sweep scheduler
   int *order;       // [4][ncell]: cells of sweep Dk in anti-diagonal order
   int has_r;
-  // FP32 correction sweeps (precision 1): correction e, FP64 defect rounded to FP32, and the
-  // frozen per-cell coefficients (u1, u2, u3, theta, dt, nu, 0, 0)
-  float *e32, *d32, *aux32;
+  // FP32 correction sweeps (precision 1): correction e, each coefficient in one 64-bit word
+  // with the version of the update that wrote it (low half the float, high half the version),
+  // FP64 defect rounded to FP32, and the frozen per-cell coefficients (u1, u2, u3, theta, dt,
+  // nu, 0, 0)
+  unsigned long long *et;
+  float *d32, *aux32;
   float *s32;  // FP32 copy of the state's coefficients: the frozen limiter weights of the correction
   // Non-uniform grid (nrmg_set_spacing; uniform = 1 leaves these NULL and uses dx, dy): widths
   // hx[nx], hy[ny] and their inverses, and per column (row) the factors of the second-order
@@ -48,6 +51,8 @@ struct Consts {
   int M, N, NP;
   int NE;      // number of multi-indices with even alpha_3 (the only nonzero ones of a planar state)
   int iq_off;  // offset in tab_i32 of the heat-flux and stress indices
+  int ln_off;  // offset in tab_i32 of the index lines of directions 0, 1, 2 (nl[d] entries each)
+  int nl[3];
   int reach;   // stencil reach: 1 (first order) or 2 (second order)
   int slope;   // 0 none, 1 central, 2 van Albada
   int model;
@@ -57,7 +62,8 @@ struct Consts {
   double lx, ly;
   double wall_u[4][3], wall_theta[4];
   // tables (global memory, copied to shared memory by each CTA)
-  const int *tab_i32;   // tslot[3][NE], tshak[N] (Shakhov target or -1), iq[3][4], is[6]
+  const int *tab_i32;   // tslot[3][NE], tshak[N] (Shakhov target or -1), iq[3][4], is[6], lines
+                        // (start | length << 11, longest first, per direction)
   const uint16_t *tab_u16;  // tmem[3][N], tprev[3][N], tnext[3][N] (0xFFFF = none), tal[3][N], tdeg[N], eidx[NE]
   const double *tab_f64;    // fact[N] (alpha!)
   const double *wallW;      // [4][(M+1)^2]: W^s_{k,m}
@@ -77,6 +83,16 @@ __host__ __device__ inline int nmom_even(int M) {
   for (int a3 = 0; a3 <= M; a3 += 2) n += (M - a3 + 1) * (M - a3 + 2) / 2;
   return n;
 }
+
+// Index lines of the line-wise FP32 transform along direction d: along x and y the lines with
+// even alpha_3, along alpha_3 every line (its even entries are the outputs).
+__host__ __device__ inline int nlines(int M, int d) {
+  if (d == 2) return (M + 1) * (M + 2) / 2;
+  int n = 0;
+  for (int a3 = 0; a3 <= M; a3 += 2) n += M - a3 + 1;
+  return n;
+}
+__host__ __device__ inline int nlines_total(int M) { return nlines(M, 0) + nlines(M, 1) + nlines(M, 2); }
 
 // One problem of a batched FS launch: its scheme constants and the level being swept.
 struct BatchDesc {

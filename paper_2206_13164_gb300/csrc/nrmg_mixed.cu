@@ -16,14 +16,23 @@
 // limited operator lets some modes stop contracting: the iteration then stalls near 1e-6.)  Because the unknown is the correction, its FP32 rounding error is relative
 // to e, which shrinks with the defect: the outer FP64 iteration converges to the FP64 fixed
 // point R(f) = r.
+//
+// The correction sweep is bound by the latency of the chain of dependent cell updates, not by
+// FP32 arithmetic.  Two things keep global-memory round trips off that chain: each correction
+// coefficient travels in one 64-bit word together with the version of the update that wrote it
+// (so the data is its own ready flag: no release fence, no flag load before the data load), and
+// everything that stays fixed during the launch (frozen coefficients, FP32 state, the defect) is
+// copied into shared memory asynchronously while the dependencies are still pending.
 #include "nrmg_device.cuh"
 
 namespace nrmg {
 
 // ------------------------------------------------------------------ shared-memory layout (FP32)
 struct CLayout {
-  size_t cst, VA, VB, ss, vsrc, vdst, cf, sc, ti32, vflag, iarr, tu16, total;
+  size_t cst, VA, VB, ss, dd, vsrc, vdst, cf, sc, ti32, vflag, iarr, tu16, wl, total;
 };
+// FP32 wall tables in shared memory: W [4][(M+1)^2], rho weights [4][M+1], incoming [4][M+1]
+__host__ __device__ inline int wall_floats(int M) { return 4 * (M + 1) * (M + 1) + 8 * (M + 1); }
 
 __host__ __device__ inline CLayout make_corr_layout(int M, int N, int NP) {
   const int NE = nmom_even(M);
@@ -35,14 +44,16 @@ __host__ __device__ inline CLayout make_corr_layout(int M, int N, int NP) {
   s.VA = o;    o = al16(o + sizeof(float) * kNV * NP);
   s.VB = o;    o = al16(o + sizeof(float) * vb);
   s.ss = o;    o = al16(o + sizeof(float) * 9 * NP);
+  s.dd = o;    o = al16(o + sizeof(float) * NP);
   s.vsrc = o;  o = al16(o + sizeof(float) * kNV * 4);
   s.vdst = o;  o = al16(o + sizeof(float) * kNV * 4);
   s.cf = o;    o = al16(o + sizeof(float) * kNV * 3 * (M + 1));
   s.sc = o;    o = al16(o + sizeof(float) * 64);
-  s.ti32 = o;  o = al16(o + sizeof(int) * (3 * NE + N));
+  s.ti32 = o;  o = al16(o + sizeof(int) * (3 * NE + N + 18 + nlines_total(M)));
   s.vflag = o; o = al16(o + sizeof(int) * kNV * 3);
   s.iarr = o;  o = al16(o + sizeof(int) * 64);
   s.tu16 = o;  o = al16(o + sizeof(uint16_t) * (13 * N + NE));
+  s.wl = o;    o = al16(o + sizeof(float) * wall_floats(M));
   s.total = o;
   return s;
 }
@@ -79,6 +90,92 @@ __device__ inline float *cstencil(const SmT<float> &s, int sl, int NP) {
 __device__ inline float *corr_state(char *base, int M, int N, int NP) {
   return (float *)(base + make_corr_layout(M, N, NP).ss);
 }
+// the updated cell's FP32 defect row
+__device__ inline float *corr_defect(char *base, int M, int N, int NP) {
+  return (float *)(base + make_corr_layout(M, N, NP).dd);
+}
+
+// ------------------------------------------------------------------ tagged correction words
+// Each coefficient of the correction is one 64-bit word: the FP32 value in the low half, the
+// version of the update that wrote it in the high half.  A naturally aligned 64-bit access is
+// single-copy atomic, so a reader that sees the version it needs also sees that update's value:
+// the word itself is the flag, and neither a fence on the writer's side nor a separate flag
+// load on the reader's side sits between two dependent updates.
+__device__ inline unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ inline unsigned long long tag_word(float x, int version) {
+  return ((unsigned long long)(unsigned)version << 32) | (unsigned long long)__float_as_uint(x);
+}
+__device__ inline int word_version(unsigned long long w) { return (int)(unsigned)(w >> 32); }
+__device__ inline float word_value(unsigned long long w) { return __uint_as_float((unsigned)w); }
+
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned)
+__device__ inline void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// One warp copies the even-alpha_3 entries of a cell's correction row (src, NP words) into
+// dst once each word carries version `need` or newer.  Every lane keeps its unsatisfied words
+// and re-reads them (the loop is warp-uniform); lane 0 watches the abort flag and the time
+// limit.  Returns false when the wait gave up.
+__device__ inline bool ll_row(const Consts &K, const uint16_t *eidx, const unsigned long long *src, float *dst,
+                              int need, int lane) {
+  constexpr int kU = 8;
+  const int NE = K.NE;
+  unsigned long long t0 = 0;
+  for (int b = 0; b < NE; b += kU * 32) {
+    unsigned long long w[kU];
+    int o[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = b + lane + u * 32;
+      o[u] = e < NE ? (int)eidx[e] : -1;
+      if (o[u] >= 0) w[u] = ld_relaxed_u64(src + o[u]);
+    }
+    unsigned pend = 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (o[u] >= 0) {
+        if (word_version(w[u]) >= need)
+          dst[o[u]] = word_value(w[u]);
+        else
+          pend |= 1u << u;
+      }
+    while (__any_sync(0xffffffffu, pend != 0)) {
+      int stop = 0;
+      if (lane == 0) {
+        if (t0 == 0) t0 = gtimer();
+        if (ld_volatile(K.abort_flag)) {
+          stop = 1;
+        } else if (gtimer() - t0 > kWaitLimitNs) {
+          raise_status(K, kStTimeout, true);
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+      __nanosleep(32);
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if ((pend >> u) & 1u) {
+          const unsigned long long x = ld_relaxed_u64(src + o[u]);
+          if (word_version(x) >= need) {
+            dst[o[u]] = word_value(x);
+            pend &= ~(1u << u);
+          }
+        }
+    }
+  }
+  return true;
+}
 
 // half of the limited slope of the frozen face bases (FP32 twin of the FP64 reconstruction)
 __device__ inline float half_slope_f(int slope, float qm, float q0, float qp) {
@@ -90,12 +187,119 @@ __device__ inline float half_slope_f(int slope, float qm, float q0, float qp) {
 
 enum { C_DT = 0, C_NU = 1, C_Q = 2 /* ..5 */, C_W = 8 /* ..8+12 */, C_RHOW = 20 /* ..24 */ };
 
+// ------------------------------------------------------------------ line-wise FP32 basis transform
+// g = prod_d exp(-a_d S_d - b S_d^2) f for the active vectors, as the FP64 transform, but with
+// one thread per (vector, index line): the thread holds the line's inputs and the direction's
+// series coefficients in registers and forms every output of the line, y_n = sum_{k<=n} c_k
+// x_{n-k} (n = position along the line), so no output waits on a chain of shared-memory index
+// loads.  Along alpha_3 only the even entries take part: a_3 = 0 for planar states, so the odd
+// coefficients c_k vanish and even outputs only see even inputs.  Lines are ordered longest
+// first; passes X->Y, Y->X, X->Y.
+// Each output sums its terms in two partial sums in ascending k, as transform_one does (a
+// nonzero a: odd k in the first, even k >= 2 in the second; a = 0: the odd c_k vanish and k = 2
+// mod 4 goes to the first, k = 0 mod 4 to the second), so both transforms round alike.
+template <int kLmax>
+__device__ inline void line_xy(const float *x, float *y, const float *c, const uint16_t *m, int L, int fl) {
+  float a0[kLmax], a1[kLmax], xv[kLmax];
+  int id[kLmax];
+#pragma unroll
+  for (int q = 0; q < kLmax; ++q) {
+    id[q] = q < L ? m[q] : 0;
+    xv[q] = q < L ? x[id[q]] : 0.0f;
+    a0[q] = xv[q];
+    a1[q] = 0.0f;
+  }
+  if (!(fl & 1)) {
+    const bool zero_a = fl & 2;
+#pragma unroll
+    for (int k = 1; k < kLmax; ++k) {
+      if (k >= L) break;
+      if (zero_a && (k & 1)) continue;
+      const float ck = c[k];
+      const bool first = zero_a ? (k & 3) == 2 : (k & 1);
+#pragma unroll
+      for (int n = k; n < kLmax; ++n) {
+        if (first)
+          a0[n] = fmaf(ck, xv[n - k], a0[n]);
+        else
+          a1[n] = fmaf(ck, xv[n - k], a1[n]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kLmax; ++q)
+    if (q < L) y[id[q]] = a0[q] + a1[q];
+}
+
+// along alpha_3: even entries only (position 2n holds alpha_3 = 2n); c_{2j} with j odd in the
+// first partial sum, j even in the second
+template <int kLmax>
+__device__ inline void line_z(const float *x, float *y, const float *c, const uint16_t *m, int L, int fl) {
+  constexpr int kE = (kLmax + 1) / 2;
+  const int Le = (L + 1) / 2;
+  float a0[kE], a1[kE], xv[kE];
+  int id[kE];
+#pragma unroll
+  for (int q = 0; q < kE; ++q) {
+    id[q] = q < Le ? m[2 * q] : 0;
+    xv[q] = q < Le ? x[id[q]] : 0.0f;
+    a0[q] = xv[q];
+    a1[q] = 0.0f;
+  }
+  if (!(fl & 1)) {
+#pragma unroll
+    for (int k = 1; k < kE; ++k) {
+      if (k >= Le) break;
+      const float ck = c[2 * k];
+#pragma unroll
+      for (int n = k; n < kE; ++n) {
+        if (k & 1)
+          a0[n] = fmaf(ck, xv[n - k], a0[n]);
+        else
+          a1[n] = fmaf(ck, xv[n - k], a1[n]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kE; ++q)
+    if (q < Le) y[id[q]] = a0[q] + a1[q];
+}
+
+// longest index line of the line-wise transform (M <= kLineMax - 1; higher orders use the
+// output-wise transform_batch)
+constexpr int kLineMax = 11;
+
+__device__ inline void transform_lines(const Consts &K, SmT<float> &s, const int *lines, float *X, float *Y) {
+  const int N = K.N, NP = K.NP, M = K.M, na = s.iarr[I_NACT];
+  const int *ln = lines;
+  for (int d = 0; d < 3; ++d) {
+    const float *in = (d == 1) ? Y : X;
+    float *out = (d == 1) ? X : Y;
+    const int nl = K.nl[d], tot = na * nl;
+    const uint16_t *mem = s.tmem + d * N;
+    for (int t = threadIdx.x; t < tot; t += kThreads) {
+      const int l = t / na, vi = t - l * na;
+      const int v = s.iarr[I_ACT + vi];
+      const int code = ln[l], L = code >> 11;
+      const uint16_t *m = mem + (code & 2047);
+      const float *c = s.cf + (v * 3 + d) * (M + 1);
+      const int fl = s.vflag[v * 3 + d];
+      if (d < 2)
+        line_xy<kLineMax>(in + v * NP, out + v * NP, c, m, L, fl);
+      else
+        line_z<kLineMax>(in + v * NP, out + v * NP, c, m, L, fl);
+    }
+    ln += nl;
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ frozen coefficients and FP32 defect
 __global__ void mixed_prep_kernel(Consts K, LevelDev L) {
   const size_t tot = (size_t)L.ncell * K.NP;
   for (size_t q = (size_t)blockIdx.x * kThreads + threadIdx.x; q < tot; q += (size_t)gridDim.x * kThreads) {
     L.d32[q] = (float)L.D[q];
-    L.e32[q] = 0.0f;
+    L.et[q] = 0ull;  // e = 0, version 0
     L.s32[q] = (float)L.F[q];
   }
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < L.ncell; c += gridDim.x * kThreads) {
@@ -119,12 +323,25 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
   SmT<float> s = bind_corr(smem_raw, K.M, K.N, K.NP);
   float *ss = corr_state(smem_raw, K.M, K.N, K.NP);
   const int tid = threadIdx.x, N = K.N, NP = K.NP, NE = K.NE, M = K.M;
-  for (int e = tid; e < 3 * NE + N; e += kThreads) s.tslot[e] = K.tab_i32[e];
+  // constant tables: index tables and lines, the FP32 wall tables
+  const int ni32 = K.ln_off + nlines_total(M);
+  for (int e = tid; e < ni32; e += kThreads) s.tslot[e] = K.tab_i32[e];
   for (int e = tid; e < 13 * N + NE; e += kThreads) s.tmem[e] = K.tab_u16[e];
+  float *wl = (float *)(smem_raw + make_corr_layout(M, N, NP).wl);
+  float *wW = wl, *wR = wl + 4 * (M + 1) * (M + 1), *wIn = wR + 4 * (M + 1);
+  for (int e = tid; e < 4 * (M + 1) * (M + 1); e += kThreads) wW[e] = K.wallWf[e];
+  for (int e = tid; e < 4 * (M + 1); e += kThreads) {
+    wR[e] = K.wallRf[e];
+    wIn[e] = K.wallInf[e];
+  }
   __syncthreads();
+  const int *lines = s.tslot + K.ln_off;
+  const int *iqs = s.tslot + K.iq_off;  // heat-flux indices [3][4], then idx(e_i + e_j)
+  const int i12 = iqs[12 + 1];
   const int ncell = L.ncell;
   const long long total = (long long)steps * 4 * ncell;
   const float Cf = (float)K.C;
+  float *dsm = corr_defect(smem_raw, M, N, NP);
   for (;;) {
     if (tid == 0) {
       int it = atomicAdd(K.queue, 1);
@@ -148,12 +365,14 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     }
     const int i = c % L.nx, j = c / L.nx;
     const int v = 4 * st + k + 1;
-    // ---- per stencil slot (warp w takes slot w, warp 0 also slot 8): lane 0 waits until the
-    //      cell holds the version of the serial order (the newest for a neighbour that sweep Dk
-    //      visits earlier, the previous one otherwise), then the warp loads the cell's row:
-    //      frozen coefficients, correction and FP32 state (even alpha_3 entries, kU loads in
-    //      flight per lane).  A satisfied cell cannot change again before this update is
-    //      published, so rows that are ready early load while the last dependency is pending.
+    // ---- the data that stays fixed during the launch (the cell's defect row; each stencil
+    //      cell's frozen coefficients and FP32 state) is copied asynchronously at once; then
+    //      per stencil slot (warp w takes slot w, warp 0 also slot 8) the warp waits until the
+    //      cell's correction words carry the version of the serial order (the newest for a
+    //      neighbour that sweep Dk visits earlier, the previous one otherwise) and copies them.
+    //      A satisfied cell cannot change again before this update is published, so rows that
+    //      are ready early load while the last dependency is pending.
+    for (int q = tid; q < NP / 4; q += kThreads) cp_async16(dsm + 4 * q, L.d32 + (size_t)c * NP + 4 * q);
     {
       const int warp = tid >> 5, lane = tid & 31;
       const int si = (k == 0 || k == 3) ? 1 : -1, sj = (k == 0 || k == 1) ? 1 : -1;
@@ -161,146 +380,111 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         const int di = c_nb_di[sl], dj = c_nb_dj[sl];
         const int ii = i + di, jj = j + dj;
         const bool in = ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny && abs(di) + abs(dj) <= K.reach;
-        int ok = 0;
         if (lane == 0) {
           s.iarr[I_EX + sl] = in ? 1 : 0;
           if (sl >= 1 && sl <= 4) s.iarr[I_WALL + sl - 1] = in ? 0 : 1;  // face f = slot f + 1
-          if (in) {
-            const bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
-            const int need = (sl != 0 && before) ? v : v - 1;
-            const int *flag = L.ver + (size_t)jj * L.nx + ii;
-            ok = 1;
-            if (ld_acquire(flag) < need) {
-              unsigned long long t0 = gtimer();
-              while (ld_acquire(flag) < need) {
-                if (ld_volatile(K.abort_flag)) {
-                  ok = 0;
-                  break;
-                }
-                if (gtimer() - t0 > kWaitLimitNs) {
-                  raise_status(K, kStTimeout, true);
-                  ok = 0;
-                  break;
-                }
-                __nanosleep(32);
-              }
-            }
-            if (!ok) s.iarr[I_ABW] = 1;
-          }
         }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (ok) {
-          const int cc = c + dj * L.nx + di;
-          float *row = cstencil(s, sl, NP), *srow = ss + sl * NP;
-          const int W = 8 + 2 * NE;
-          constexpr int kU = 8;
-          for (int q0 = lane; q0 < W; q0 += kU * 32) {
-            float vv[kU];
-            float *dd[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-              const int e = q0 + u * 32;
-              dd[u] = nullptr;
-              if (e < 8) {
-                vv[u] = __ldcg(L.aux32 + (size_t)cc * 8 + e);
-                dd[u] = row + e;
-              } else if (e < 8 + NE) {
-                const int o = s.eidx[e - 8];
-                vv[u] = __ldcg(L.e32 + (size_t)cc * NP + o);
-                dd[u] = row + 8 + o;
-              } else if (e < W) {
-                const int o = s.eidx[e - 8 - NE];
-                vv[u] = L.s32[(size_t)cc * NP + o];  // written before the launch
-                dd[u] = srow + o;
-              }
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-              if (dd[u]) *dd[u] = vv[u];
-          }
-        }
+        if (!in) continue;  // warp-uniform
+        const int cc = c + dj * L.nx + di;
+        float *row = cstencil(s, sl, NP), *srow = ss + sl * NP;
+        if (lane < 2) cp_async16(row + 4 * lane, L.aux32 + (size_t)cc * 8 + 4 * lane);
+        for (int q = lane; q < NP / 4; q += 32) cp_async16(srow + 4 * q, L.s32 + (size_t)cc * NP + 4 * q);
+        const bool before = (si * di < 0) || (di == 0 && sj * dj < 0);
+        const int need = (sl != 0 && before) ? v : v - 1;
+        if (!ll_row(K, s.eidx, L.et + (size_t)cc * NP, row + 8, need, lane) && lane == 0) s.iarr[I_ABW] = 1;
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     if (s.iarr[I_ABW]) break;
     const float *ac = s.cst, *ec = s.cst + 8;  // own frozen coefficients, own correction
     // ---- face states of the correction, slots as in the FP64 operator: 2f / 2f+1 = face f's
-    //      left / right state (E, W, N, S), or 2f = the cell in the wall basis at a wall
+    //      left / right state (E, W, N, S), or 2f = the cell in the wall basis at a wall.  One
+    //      thread per element (e < 4: the frozen params, which give the face bases; else the
+    //      correction coefficient eidx[e - 4]) forms that element of every face state.
     {
+      unsigned ex = 0;
+#pragma unroll
+      for (int sl = 0; sl < 9; ++sl) ex |= (s.iarr[I_EX + sl] ? 1u : 0u) << sl;
+      const bool wallW = s.iarr[I_WALL + 1], wallS = s.iarr[I_WALL + 3];
       const bool slopes = K.reach == 2 && K.slope != 0;
-      const int tot = 6 * (4 + NE);
-      for (int q = tid; q < tot; q += kThreads) {
-        int it = q / (4 + NE), e = q - it * (4 + NE);
-        int X = c_it_x[it], Xm = c_it_m[it], Xp = c_it_p[it];
-        if (!s.iarr[I_EX + X]) continue;
-        bool on = slopes && s.iarr[I_EX + Xm] && s.iarr[I_EX + Xp];
-        const float *rx = cstencil(s, X, NP);
-        // reconstruction factors of the item's cell: 1, 1, 1/4 on a uniform grid
-        float rm = 1.0f, rp = 1.0f, ch = 0.25f;
-        if (on && !L.uniform) {
-          if (it == 1 || it >= 4) {
-            const int r = j + c_nb_dj[X];
-            rm = (float)L.rmy[r], rp = (float)L.rpy[r], ch = (float)L.chy[r];
-          } else {
-            const int col = i + c_nb_di[X];
-            rm = (float)L.rmx[col], rp = (float)L.rpx[col], ch = (float)L.chx[col];
-          }
+      for (int e = tid; e < 4 + NE; e += kThreads) {
+        const bool par = e < 4;
+        const int o = par ? e : s.eidx[e - 4];
+        const int col = par ? e : 8 + o;
+        float q[9], w[9];
+#pragma unroll
+        for (int sl = 0; sl < 9; ++sl) {
+          q[sl] = ((ex >> sl) & 1u) ? cstencil(s, sl, NP)[col] : 0.0f;
+          w[sl] = (!par && ((ex >> sl) & 1u)) ? ss[sl * NP + o] : 0.0f;
         }
-        float q0, hs = 0.0f;
-        if (e < 4) {  // face basis: the reconstructed params of the state
-          q0 = rx[e];
+        // slope items: 0 C along x, 1 C along y, 2 E, 3 W, 4 N, 5 S (cell X, lower Xm, upper Xp)
+        constexpr int itx[6] = {0, 0, 1, 2, 3, 4}, itm[6] = {2, 4, 0, 6, 0, 8}, itp[6] = {1, 3, 5, 0, 7, 0};
+#pragma unroll
+        for (int it = 0; it < 6; ++it) {
+          const int X = itx[it], Xm = itm[it], Xp = itp[it];
+          if (!((ex >> X) & 1u)) continue;
+          const bool on = slopes && ((ex >> Xm) & 1u) && ((ex >> Xp) & 1u);
+          const float q0 = q[X];
+          float hs = 0.0f;
           if (on) {
-            const float qm = cstencil(s, Xm, NP)[e], qp = cstencil(s, Xp, NP)[e];
-            hs = L.uniform ? half_slope_f(K.slope, qm, q0, qp)
-                           : (K.slope == 1 ? (qp - qm) * ch : half_slope_f(K.slope, q0 - (q0 - qm) * rm, q0, q0 + (qp - q0) * rp));
-          }
-        } else {      // correction: the limited slope linearized with frozen weights
-          e = 4 + s.eidx[e - 4];
-          const int o = e - 4;
-          q0 = rx[8 + o];
-          if (on) {
-            const float em = cstencil(s, Xm, NP)[8 + o], ep = cstencil(s, Xp, NP)[8 + o];
-            if (K.slope == 1) {
-              hs = L.uniform ? 0.25f * (ep - em) : (ep - em) * ch;
+            // reconstruction factors of the item's cell: 1, 1, 1/4 on a uniform grid
+            float rm = 1.0f, rp = 1.0f, ch = 0.25f;
+            if (!L.uniform) {
+              if (it == 1 || it >= 4) {
+                const int r = j + c_nb_dj[X];
+                rm = (float)L.rmy[r], rp = (float)L.rpy[r], ch = (float)L.chy[r];
+              } else {
+                const int cl = i + c_nb_di[X];
+                rm = (float)L.rmx[cl], rp = (float)L.rpx[cl], ch = (float)L.chx[cl];
+              }
+            }
+            const float qm = q[Xm], qp = q[Xp];
+            if (par) {  // face basis: the reconstructed params of the state
+              hs = L.uniform ? half_slope_f(K.slope, qm, q0, qp)
+                             : (K.slope == 1 ? (qp - qm) * ch
+                                             : half_slope_f(K.slope, q0 - (q0 - qm) * rm, q0, q0 + (qp - q0) * rp));
+            } else if (K.slope == 1) {  // correction: the limited slope linearized with frozen weights
+              hs = L.uniform ? 0.25f * (qp - qm) : (qp - qm) * ch;
             } else if (L.uniform) {
-              const float a = ss[X * NP + o] - ss[Xm * NP + o], b = ss[Xp * NP + o] - ss[X * NP + o];
+              const float a = w[X] - w[Xm], b = w[Xp] - w[X];
               const float den = fmaf(a, a, fmaf(b, b, 2e-12f));
-              hs = __fdividef(0.5f * (fmaf(b, b, 1e-12f) * (q0 - em) + fmaf(a, a, 1e-12f) * (ep - q0)), den);
+              hs = __fdividef(0.5f * (fmaf(b, b, 1e-12f) * (q0 - qm) + fmaf(a, a, 1e-12f) * (qp - q0)), den);
             } else {
-              const float a = (ss[X * NP + o] - ss[Xm * NP + o]) * rm, b = (ss[Xp * NP + o] - ss[X * NP + o]) * rp;
+              const float a = (w[X] - w[Xm]) * rm, b = (w[Xp] - w[X]) * rp;
               const float den = fmaf(a, a, fmaf(b, b, 2e-12f));
-              hs = __fdividef(0.5f * (fmaf(b, b, 1e-12f) * (q0 - em) * rm + fmaf(a, a, 1e-12f) * (ep - q0) * rp), den);
+              hs = __fdividef(0.5f * (fmaf(b, b, 1e-12f) * (q0 - qm) * rm + fmaf(a, a, 1e-12f) * (qp - q0) * rp), den);
             }
           }
-        }
-        int v0, v1 = -1;
-        float x0, x1 = 0.0f;
-        switch (it) {
-          case 0:
-            v0 = 0; x0 = q0 + hs;
-            if (s.iarr[I_WALL + 1]) { v1 = 2; x1 = q0; } else { v1 = 3; x1 = q0 - hs; }
-            break;
-          case 1:
-            v0 = 4; x0 = q0 + hs;
-            if (s.iarr[I_WALL + 3]) { v1 = 6; x1 = q0; } else { v1 = 7; x1 = q0 - hs; }
-            break;
-          case 2: v0 = 1; x0 = q0 - hs; break;
-          case 3: v0 = 2; x0 = q0 + hs; break;
-          case 4: v0 = 5; x0 = q0 - hs; break;
-          default: v0 = 6; x0 = q0 + hs; break;
-        }
-        if (e < 4) {
-          s.vsrc[v0 * 4 + e] = x0;
-          if (v1 >= 0) s.vsrc[v1 * 4 + e] = x1;
-        } else {
-          s.VA[v0 * NP + e - 4] = x0;
-          if (v1 >= 0) s.VA[v1 * NP + e - 4] = x1;
+          int v0, v1 = -1;
+          float x0, x1 = 0.0f;
+          switch (it) {
+            case 0:
+              v0 = 0; x0 = q0 + hs;
+              if (wallW) { v1 = 2; x1 = q0; } else { v1 = 3; x1 = q0 - hs; }
+              break;
+            case 1:
+              v0 = 4; x0 = q0 + hs;
+              if (wallS) { v1 = 6; x1 = q0; } else { v1 = 7; x1 = q0 - hs; }
+              break;
+            case 2: v0 = 1; x0 = q0 - hs; break;
+            case 3: v0 = 2; x0 = q0 + hs; break;
+            case 4: v0 = 5; x0 = q0 - hs; break;
+            default: v0 = 6; x0 = q0 + hs; break;
+          }
+          if (par) {
+            s.vsrc[v0 * 4 + e] = x0;
+            if (v1 >= 0) s.vsrc[v1 * 4 + e] = x1;
+          } else {
+            s.VA[v0 * NP + o] = x0;
+            if (v1 >= 0) s.VA[v1 * NP + o] = x1;
+          }
         }
       }
     }
     // destination bases: the cell, or the wall for a wall face's slot 2f
-    if (tid < 32) {
-      int vv = tid >> 2, e = tid & 3, f = vv >> 1;
+    if (tid >= 192 && tid < 224) {
+      int vv = (tid - 192) >> 2, e = tid & 3, f = vv >> 1;
       if (s.iarr[I_WALL + f] && !(vv & 1)) {
         int w = c_face_wall[f];
         s.vdst[vv * 4 + e] = e < 3 ? (float)K.wall_u[w][e] : (float)K.wall_theta[w];
@@ -308,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         s.vdst[vv * 4 + e] = ac[e];
       }
     }
-    if (tid == 32) {
+    if (tid == 224) {
       int na = 0;
       for (int f = 0; f < 4; ++f) {
         s.iarr[I_ACT + na++] = 2 * f;
@@ -316,9 +500,9 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       }
       s.iarr[I_NACT] = na;
     }
-    if (tid >= 96 && tid < 99 && K.model == 1) {
-      int ii = tid - 96;
-      const int *iq = K.tab_i32 + K.iq_off + 4 * ii;
+    if (tid >= 228 && tid < 231 && K.model == 1) {
+      int ii = tid - 228;
+      const int *iq = iqs + 4 * ii;
       float qv = 2.0f * ec[iq[0]];
       for (int d = 0; d < 3; ++d) qv += ec[iq[1 + d]];
       s.sc[C_Q + ii] = (ii == 2) ? 0.0f : qv;  // q_3 involves only odd alpha_3 entries
@@ -345,12 +529,15 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     }
     setup_coeffs(K, s);
     __syncthreads();
-    transform_batch(K, s, s.VA, s.VB);
+    if (M < kLineMax)
+      transform_lines(K, s, lines, s.VA, s.VB);
+    else
+      transform_batch(K, s, s.VA, s.VB);
     // ---- wall fluxes (linear in the face state)
     if (tid < 4 && s.iarr[I_WALL + tid]) {
       int w = c_face_wall[tid], ax = c_wall_axis[w];
       const float *a = s.VB + (2 * tid) * NP;
-      const float *wr = K.wallRf + w * (M + 1);
+      const float *wr = wR + w * (M + 1);
       float rw = 0.0f;
       for (int m = 0; m <= M; ++m) rw = fmaf(wr[m], a[K.idx_axis[ax][m]], rw);
       s.sc[C_RHOW + tid] = rw;
@@ -368,11 +555,11 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         int b0 = s0 - p, deg = s.tdeg[o];
         int Lm = M - (deg - p);
         const float *a = s.VB + (2 * f) * NP;
-        const float *Wm = K.wallWf + (size_t)w * (M + 1) * (M + 1) + p * (M + 1);
+        const float *Wm = wW + (size_t)w * (M + 1) * (M + 1) + p * (M + 1);
         const uint16_t *mem = s.tmem + ax * N;
         float g = 0.0f;
         for (int m = 0; m <= Lm; ++m) g = fmaf(a[mem[b0 + m]], Wm[m], g);
-        if (deg == p) g = fmaf(s.sc[C_RHOW + f], K.wallInf[w * (M + 1) + p], g);
+        if (deg == p) g = fmaf(s.sc[C_RHOW + f], wIn[w * (M + 1) + p], g);
         s.VA[(2 * f) * NP + o] = g;
       }
       if (tid == 0) {
@@ -390,7 +577,10 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       if (nw > 0) {
         setup_coeffs(K, s);
         __syncthreads();
-        transform_batch(K, s, s.VA, s.VB);
+        if (M < kLineMax)
+          transform_lines(K, s, lines, s.VA, s.VB);
+        else
+          transform_batch(K, s, s.VA, s.VB);
       }
     }
     // ---- flux differences: F_E - F_W = Xi_x d_x + e_x, F_N - F_S = Xi_y d_y + e_y
@@ -424,9 +614,7 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
     // ES-BGK: the degree-2 part of f^E is (1 - 1/Pr) times the trace-free degree-2 part of f
     // exactly; its degree >= 4 part is quadratic in the stress and is left out of the response
     const float esk = (float)(1.0 - 1.0 / K.Pr);
-    const int i12 = K.tab_i32[K.iq_off + 12 + 1];
-    float *Eo = L.e32 + (size_t)c * NP;
-    const float *Do = L.d32 + (size_t)c * NP;
+    unsigned long long *Eo = L.et + (size_t)c * NP;
     for (int q = tid; q < NE; q += kThreads) {
       const int o = s.eidx[q];
       float xi[2];
@@ -452,10 +640,10 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         if (t >= 0) pe = fmaf(shk, s.sc[C_Q + t], pe);
       }
       float R = fmaf(-(xi[0] + eX[o]), idx, fmaf(-(xi[1] + eY[o]), idy, nu * (pe - ec[o])));
-      Eo[o] = fmaf(dt, R - Do[o], ec[o]);
+      // the tagged word publishes the value: no barrier or release store follows (the next
+      // item's first barrier keeps this item's shared memory until every thread is done)
+      st_relaxed_u64(Eo + o, tag_word(fmaf(dt, R - dsm[o], ec[o]), v));
     }
-    __syncthreads();  // orders the correction's writes before the release store
-    if (tid == 0) st_release(L.ver + c, v);
   }
 }
 
@@ -536,7 +724,7 @@ __global__ void __launch_bounds__(kThreads) mixed_update_kernel(Consts K, LevelD
   for (int c = blockIdx.x; c < L.ncell; c += gridDim.x) {
     for (int q = tid; q < NE; q += kThreads) {
       const int o = s.eidx[q];
-      s.VA[o] = L.F[(size_t)c * NP + o] + (double)L.e32[(size_t)c * NP + o];
+      s.VA[o] = L.F[(size_t)c * NP + o] + (double)word_value(L.et[(size_t)c * NP + o]);
     }
     __syncthreads();
     double pc[4];
