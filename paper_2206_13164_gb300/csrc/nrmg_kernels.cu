@@ -479,9 +479,11 @@ __device__ inline void fs_wait_load(const Consts &K, const LevelDev &L, Sm &s, i
           const int *flag = L.ver + (size_t)jj * L.nx + ii;
           ok = 1;
           if (ld_acquire(flag) < need) {
+            // one load latency per round: the abort word (another global load) is read on
+            // every 16th round only, the time limit on every round
             unsigned long long t0 = gtimer();
-            while (ld_acquire(flag) < need) {
-              if (ld_volatile(K.abort_flag)) {
+            for (int it = 1; ld_acquire(flag) < need; ++it) {
+              if ((it & 15) == 0 && ld_volatile(K.abort_flag)) {
                 ok = 0;
                 break;
               }
@@ -490,7 +492,6 @@ __device__ inline void fs_wait_load(const Consts &K, const LevelDev &L, Sm &s, i
                 ok = 0;
                 break;
               }
-              __nanosleep(32);
             }
           }
           if (!ok) s.iarr[I_ABW] = 1;

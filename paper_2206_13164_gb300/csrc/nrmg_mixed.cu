@@ -31,6 +31,13 @@ namespace nrmg {
 struct CLayout {
   size_t cst, VA, VB, ss, dd, vsrc, vdst, cf, sc, ti32, vflag, iarr, tu16, wl, total;
 };
+// Longest index line of the line-wise transform (M <= kLineMax - 1; higher orders use the
+// output-wise transform_batch of the FP64 path).
+constexpr int kLineMax = 11;
+// Row stride of the transform vectors in shared memory: NP + 1 for the line-wise transform, so
+// that the lanes that take one index line of several vectors hit distinct banks (NP is a
+// multiple of 4, and of 32 for some orders); NP for transform_batch.
+__host__ __device__ inline int corr_vstride(int M, int NP) { return M < kLineMax ? NP + 1 : NP; }
 // FP32 wall tables in shared memory: W [4][(M+1)^2], rho weights [4][M+1], incoming [4][M+1]
 __host__ __device__ inline int wall_floats(int M) { return 4 * (M + 1) * (M + 1) + 8 * (M + 1); }
 
@@ -38,10 +45,10 @@ __host__ __device__ inline CLayout make_corr_layout(int M, int N, int NP) {
   const int NE = nmom_even(M);
   CLayout s;
   size_t o = 0;
-  size_t vb = (size_t)8 * (8 + NP), va = (size_t)kNV * NP;
+  size_t vb = (size_t)8 * (8 + NP), va = (size_t)kNV * corr_vstride(M, NP);
   if (va > vb) vb = va;
   s.cst = o;   o = al16(o + sizeof(float) * (8 + NP));
-  s.VA = o;    o = al16(o + sizeof(float) * kNV * NP);
+  s.VA = o;    o = al16(o + sizeof(float) * va);
   s.VB = o;    o = al16(o + sizeof(float) * vb);
   s.ss = o;    o = al16(o + sizeof(float) * 9 * NP);
   s.dd = o;    o = al16(o + sizeof(float) * NP);
@@ -150,11 +157,13 @@ __device__ inline bool ll_row(const Consts &K, const uint16_t *eidx, const unsig
         else
           pend |= 1u << u;
       }
-    while (__any_sync(0xffffffffu, pend != 0)) {
+    for (int it = 0; __any_sync(0xffffffffu, pend != 0); ++it) {
+      // the time limit is checked on every round, the abort word (a global load) on every
+      // 16th, so that a round costs one load latency
       int stop = 0;
       if (lane == 0) {
         if (t0 == 0) t0 = gtimer();
-        if (ld_volatile(K.abort_flag)) {
+        if ((it & 15) == 15 && ld_volatile(K.abort_flag)) {
           stop = 1;
         } else if (gtimer() - t0 > kWaitLimitNs) {
           raise_status(K, kStTimeout, true);
@@ -162,7 +171,6 @@ __device__ inline bool ll_row(const Consts &K, const uint16_t *eidx, const unsig
         }
       }
       if (__shfl_sync(0xffffffffu, stop, 0)) return false;
-      __nanosleep(32);
 #pragma unroll
       for (int u = 0; u < kU; ++u)
         if ((pend >> u) & 1u) {
@@ -195,99 +203,154 @@ enum { C_DT = 0, C_NU = 1, C_Q = 2 /* ..5 */, C_W = 8 /* ..8+12 */, C_RHOW = 20 
 // loads.  Along alpha_3 only the even entries take part: a_3 = 0 for planar states, so the odd
 // coefficients c_k vanish and even outputs only see even inputs.  Lines are ordered longest
 // first; passes X->Y, Y->X, X->Y.
-// Each output sums its terms in two partial sums in ascending k, as transform_one does (a
-// nonzero a: odd k in the first, even k >= 2 in the second; a = 0: the odd c_k vanish and k = 2
-// mod 4 goes to the first, k = 0 mod 4 to the second), so both transforms round alike.
-template <int kLmax>
-__device__ inline void line_xy(const float *x, float *y, const float *c, const uint16_t *m, int L, int fl) {
-  float a0[kLmax], a1[kLmax], xv[kLmax];
-  int id[kLmax];
+// One index line along x or y per lane, the warp's lines at most kL long (L <= kL per lane,
+// 0 for an idle lane): inputs, indices and series coefficients in registers; every lane runs
+// the same kL-long code (entries from L on are zero and their outputs are not stored), so the
+// warp never diverges on the line length.  Each output sums its terms in two partial sums in
+// ascending k, as transform_one does (a nonzero a: odd k in the first, even k >= 2 in the
+// second; a = 0: the odd c_k vanish, k = 2 mod 4 goes to the first, k = 0 mod 4 to the
+// second), so both transforms round alike; a warp takes the second ordering only when one of
+// its lanes has a = 0.  An identity transform (a = b = 0) adds exact zeros.
+template <int kL>
+__device__ __forceinline__ void line_xy(const float *x, float *y, const float *c, const uint16_t *m, int L, int fl,
+                                        bool any_zero_a) {
+  float a0[kL], a1[kL], xv[kL];
+  int id[kL];
+  const bool ident = fl & 1, zero_a = (fl & 2) && !ident;
 #pragma unroll
-  for (int q = 0; q < kLmax; ++q) {
-    id[q] = q < L ? m[q] : 0;
-    xv[q] = q < L ? x[id[q]] : 0.0f;
+  for (int q = 0; q < kL; ++q) id[q] = q < L ? (int)m[q] : -1;
+#pragma unroll
+  for (int q = 0; q < kL; ++q) {
+    xv[q] = id[q] >= 0 ? x[id[q]] : 0.0f;
     a0[q] = xv[q];
     a1[q] = 0.0f;
   }
-  if (!(fl & 1)) {
-    const bool zero_a = fl & 2;
+  if (!any_zero_a) {
 #pragma unroll
-    for (int k = 1; k < kLmax; ++k) {
-      if (k >= L) break;
-      if (zero_a && (k & 1)) continue;
-      const float ck = c[k];
-      const bool first = zero_a ? (k & 3) == 2 : (k & 1);
+    for (int k = 1; k < kL; ++k) {
+      const float ck = (ident || k >= L) ? 0.0f : c[k];
 #pragma unroll
-      for (int n = k; n < kLmax; ++n) {
-        if (first)
-          a0[n] = fmaf(ck, xv[n - k], a0[n]);
-        else
-          a1[n] = fmaf(ck, xv[n - k], a1[n]);
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < kLmax; ++q)
-    if (q < L) y[id[q]] = a0[q] + a1[q];
-}
-
-// along alpha_3: even entries only (position 2n holds alpha_3 = 2n); c_{2j} with j odd in the
-// first partial sum, j even in the second
-template <int kLmax>
-__device__ inline void line_z(const float *x, float *y, const float *c, const uint16_t *m, int L, int fl) {
-  constexpr int kE = (kLmax + 1) / 2;
-  const int Le = (L + 1) / 2;
-  float a0[kE], a1[kE], xv[kE];
-  int id[kE];
-#pragma unroll
-  for (int q = 0; q < kE; ++q) {
-    id[q] = q < Le ? m[2 * q] : 0;
-    xv[q] = q < Le ? x[id[q]] : 0.0f;
-    a0[q] = xv[q];
-    a1[q] = 0.0f;
-  }
-  if (!(fl & 1)) {
-#pragma unroll
-    for (int k = 1; k < kE; ++k) {
-      if (k >= Le) break;
-      const float ck = c[2 * k];
-#pragma unroll
-      for (int n = k; n < kE; ++n) {
+      for (int n = k; n < kL; ++n) {
         if (k & 1)
           a0[n] = fmaf(ck, xv[n - k], a0[n]);
         else
           a1[n] = fmaf(ck, xv[n - k], a1[n]);
       }
     }
+  } else {
+#pragma unroll
+    for (int k = 1; k < kL; ++k) {
+      const float ck = (ident || k >= L) ? 0.0f : c[k];
+      const bool first = zero_a ? (k & 3) == 2 : (k & 1);
+#pragma unroll
+      for (int n = k; n < kL; ++n) {
+        const float t = fmaf(ck, xv[n - k], first ? a0[n] : a1[n]);
+        if (first)
+          a0[n] = t;
+        else
+          a1[n] = t;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kL; ++q)
+    if (id[q] >= 0) y[id[q]] = a0[q] + a1[q];
+}
+
+// Along alpha_3 (at most kE even entries per lane, alpha_3 = 2n at position 2n of the line):
+// c_{2j} with j odd in the first partial sum, j even in the second.
+template <int kE>
+__device__ __forceinline__ void line_z(const float *x, float *y, const float *c, const uint16_t *m, int Le, int fl) {
+  float a0[kE], a1[kE], xv[kE];
+  int id[kE];
+  const bool ident = fl & 1;
+#pragma unroll
+  for (int q = 0; q < kE; ++q) id[q] = q < Le ? (int)m[2 * q] : -1;
+#pragma unroll
+  for (int q = 0; q < kE; ++q) {
+    xv[q] = id[q] >= 0 ? x[id[q]] : 0.0f;
+    a0[q] = xv[q];
+    a1[q] = 0.0f;
+  }
+#pragma unroll
+  for (int k = 1; k < kE; ++k) {
+    const float ck = (ident || k >= Le) ? 0.0f : c[2 * k];
+#pragma unroll
+    for (int n = k; n < kE; ++n) {
+      if (k & 1)
+        a0[n] = fmaf(ck, xv[n - k], a0[n]);
+      else
+        a1[n] = fmaf(ck, xv[n - k], a1[n]);
+    }
   }
 #pragma unroll
   for (int q = 0; q < kE; ++q)
-    if (q < Le) y[id[q]] = a0[q] + a1[q];
+    if (id[q] >= 0) y[id[q]] = a0[q] + a1[q];
 }
 
-// longest index line of the line-wise transform (M <= kLineMax - 1; higher orders use the
-// output-wise transform_batch)
-constexpr int kLineMax = 11;
-
-__device__ inline void transform_lines(const Consts &K, SmT<float> &s, const int *lines, float *X, float *Y) {
-  const int N = K.N, NP = K.NP, M = K.M, na = s.iarr[I_NACT];
+// g = prod_d exp(-a_d S_d - b S_d^2) f for the active vectors, as the FP64 transform, but with
+// one lane per (index line, vector): the lane holds the line's inputs and the direction's
+// series coefficients in registers and forms every output of the line, y_n = sum_{k<=n} c_k
+// x_{n-k} (n = position along the line), so no output waits on a chain of shared-memory index
+// loads.  Along alpha_3 only the even entries take part: a_3 = 0 for planar states, so the odd
+// coefficients c_k vanish and even outputs only see even inputs.  Lines are ordered longest
+// first and consecutive lanes take one line of consecutive vectors, so a warp's lines have
+// similar lengths; the warp runs the code of its longest line.  Passes X->Y, Y->X, X->Y;
+// vectors VS floats apart.
+__device__ __forceinline__ void transform_lines(const Consts &K, SmT<float> &s, const int *lines, float *X, float *Y,
+                                             int VS) {
+  const int N = K.N, M = K.M, na = s.iarr[I_NACT];
+  const int lane = threadIdx.x & 31;
   const int *ln = lines;
   for (int d = 0; d < 3; ++d) {
     const float *in = (d == 1) ? Y : X;
     float *out = (d == 1) ? X : Y;
     const int nl = K.nl[d], tot = na * nl;
     const uint16_t *mem = s.tmem + d * N;
-    for (int t = threadIdx.x; t < tot; t += kThreads) {
-      const int l = t / na, vi = t - l * na;
-      const int v = s.iarr[I_ACT + vi];
-      const int code = ln[l], L = code >> 11;
-      const uint16_t *m = mem + (code & 2047);
+    for (int tb = threadIdx.x - lane; tb < tot; tb += kThreads) {  // warp-uniform loop
+      const int t = tb + lane;
+      int L = 0, fl = 1, v = 0;
+      const uint16_t *m = mem;
+      if (t < tot) {
+        const int l = t / na, vi = t - l * na;
+        v = s.iarr[I_ACT + vi];
+        const int code = ln[l];
+        L = code >> 11;
+        m = mem + (code & 2047);
+        fl = s.vflag[v * 3 + d];
+      }
       const float *c = s.cf + (v * 3 + d) * (M + 1);
-      const int fl = s.vflag[v * 3 + d];
-      if (d < 2)
-        line_xy<kLineMax>(in + v * NP, out + v * NP, c, m, L, fl);
-      else
-        line_z<kLineMax>(in + v * NP, out + v * NP, c, m, L, fl);
+      const float *x = in + v * VS;
+      float *y = out + v * VS;
+      if (d < 2) {
+        const int Lw = __reduce_max_sync(0xffffffffu, (unsigned)L);
+        const bool anyz = __any_sync(0xffffffffu, (fl & 2) && !(fl & 1) && L > 0);
+        switch (Lw) {
+          case 0: break;
+          case 1: line_xy<1>(x, y, c, m, L, fl, anyz); break;
+          case 2: line_xy<2>(x, y, c, m, L, fl, anyz); break;
+          case 3: line_xy<3>(x, y, c, m, L, fl, anyz); break;
+          case 4: line_xy<4>(x, y, c, m, L, fl, anyz); break;
+          case 5: line_xy<5>(x, y, c, m, L, fl, anyz); break;
+          case 6: line_xy<6>(x, y, c, m, L, fl, anyz); break;
+          case 7: line_xy<7>(x, y, c, m, L, fl, anyz); break;
+          case 8: line_xy<8>(x, y, c, m, L, fl, anyz); break;
+          case 9: line_xy<9>(x, y, c, m, L, fl, anyz); break;
+          case 10: line_xy<10>(x, y, c, m, L, fl, anyz); break;
+          default: line_xy<11>(x, y, c, m, L, fl, anyz); break;
+        }
+      } else {
+        const int Le = (L + 1) >> 1;
+        switch (__reduce_max_sync(0xffffffffu, (unsigned)Le)) {
+          case 0: break;
+          case 1: line_z<1>(x, y, c, m, Le, fl); break;
+          case 2: line_z<2>(x, y, c, m, Le, fl); break;
+          case 3: line_z<3>(x, y, c, m, Le, fl); break;
+          case 4: line_z<4>(x, y, c, m, Le, fl); break;
+          case 5: line_z<5>(x, y, c, m, Le, fl); break;
+          default: line_z<6>(x, y, c, m, Le, fl); break;
+        }
+      }
     }
     ln += nl;
     __syncthreads();
@@ -342,6 +405,7 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
   const long long total = (long long)steps * 4 * ncell;
   const float Cf = (float)K.C;
   float *dsm = corr_defect(smem_raw, M, N, NP);
+  const int VS = corr_vstride(M, NP);  // row stride of the transform vectors in VA / VB
   for (;;) {
     if (tid == 0) {
       int it = atomicAdd(K.queue, 1);
@@ -408,7 +472,12 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       for (int sl = 0; sl < 9; ++sl) ex |= (s.iarr[I_EX + sl] ? 1u : 0u) << sl;
       const bool wallW = s.iarr[I_WALL + 1], wallS = s.iarr[I_WALL + 3];
       const bool slopes = K.reach == 2 && K.slope != 0;
-      for (int e = tid; e < 4 + NE; e += kThreads) {
+      // coefficient lanes fill whole warps; the four params go to the next warp, so that no
+      // warp runs both kinds
+      const int ncw = (NE + 31) & ~31;
+      for (int qe = tid; qe < ncw + 4; qe += kThreads) {
+        if (qe < ncw && qe >= NE) continue;
+        const int e = qe < ncw ? 4 + qe : qe - ncw;
         const bool par = e < 4;
         const int o = par ? e : s.eidx[e - 4];
         const int col = par ? e : 8 + o;
@@ -476,8 +545,8 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
             s.vsrc[v0 * 4 + e] = x0;
             if (v1 >= 0) s.vsrc[v1 * 4 + e] = x1;
           } else {
-            s.VA[v0 * NP + o] = x0;
-            if (v1 >= 0) s.VA[v1 * NP + o] = x1;
+            s.VA[v0 * VS + o] = x0;
+            if (v1 >= 0) s.VA[v1 * VS + o] = x1;
           }
         }
       }
@@ -527,23 +596,26 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
       s.sc[C_W + 3 * f + 1] = w2;
       s.sc[C_W + 3 * f + 2] = w3;
     }
-    setup_coeffs(K, s);
-    __syncthreads();
-    if (M < kLineMax)
-      transform_lines(K, s, lines, s.VA, s.VB);
-    else
-      transform_batch(K, s, s.VA, s.VB);
-    // ---- wall fluxes (linear in the face state)
-    if (tid < 4 && s.iarr[I_WALL + tid]) {
-      int w = c_face_wall[tid], ax = c_wall_axis[w];
-      const float *a = s.VB + (2 * tid) * NP;
-      const float *wr = wR + w * (M + 1);
-      float rw = 0.0f;
-      for (int m = 0; m <= M; ++m) rw = fmaf(wr[m], a[K.idx_axis[ax][m]], rw);
-      s.sc[C_RHOW + tid] = rw;
-    }
-    __syncthreads();
-    {
+    // batch 0: face states -> cell basis and the cell -> wall bases; batch 1 (cells with a
+    // wall face): the wall fluxes -> cell basis.  One call site keeps one inlined copy.
+    for (int batch = 0;; ++batch) {
+      setup_coeffs(K, s);
+      __syncthreads();
+      if (M < kLineMax)
+        transform_lines(K, s, lines, s.VA, s.VB, VS);
+      else
+        transform_batch(K, s, s.VA, s.VB);
+      if (batch == 1) break;
+      // ---- wall fluxes (linear in the face state)
+      if (tid < 4 && s.iarr[I_WALL + tid]) {
+        int w = c_face_wall[tid], ax = c_wall_axis[w];
+        const float *a = s.VB + (2 * tid) * VS;
+        const float *wr = wR + w * (M + 1);
+        float rw = 0.0f;
+        for (int m = 0; m <= M; ++m) rw = fmaf(wr[m], a[K.idx_axis[ax][m]], rw);
+        s.sc[C_RHOW + tid] = rw;
+      }
+      __syncthreads();
       int nw = 0, wf[4];
       for (int f = 0; f < 4; ++f)
         if (s.iarr[I_WALL + f]) wf[nw++] = f;
@@ -554,13 +626,13 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         int o = pk & 2047, s0 = (pk >> 11) & 2047, p = pk >> 22;
         int b0 = s0 - p, deg = s.tdeg[o];
         int Lm = M - (deg - p);
-        const float *a = s.VB + (2 * f) * NP;
+        const float *a = s.VB + (2 * f) * VS;
         const float *Wm = wW + (size_t)w * (M + 1) * (M + 1) + p * (M + 1);
         const uint16_t *mem = s.tmem + ax * N;
         float g = 0.0f;
         for (int m = 0; m <= Lm; ++m) g = fmaf(a[mem[b0 + m]], Wm[m], g);
         if (deg == p) g = fmaf(s.sc[C_RHOW + f], wIn[w * (M + 1) + p], g);
-        s.VA[(2 * f) * NP + o] = g;
+        s.VA[(2 * f) * VS + o] = g;
       }
       if (tid == 0) {
         for (int kk = 0; kk < nw; ++kk) s.iarr[I_ACT + kk] = 2 * wf[kk];
@@ -574,14 +646,7 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         }
       }
       __syncthreads();
-      if (nw > 0) {
-        setup_coeffs(K, s);
-        __syncthreads();
-        if (M < kLineMax)
-          transform_lines(K, s, lines, s.VA, s.VB);
-        else
-          transform_batch(K, s, s.VA, s.VB);
-      }
+      if (nw == 0) break;
     }
     // ---- flux differences: F_E - F_W = Xi_x d_x + e_x, F_N - F_S = Xi_y d_y + e_y
     float *dX = s.VA, *dY = s.VA + NP, *eX = s.VA + 2 * NP, *eY = s.VA + 3 * NP;
@@ -593,9 +658,9 @@ __global__ void __launch_bounds__(kThreads) fs_corr_kernel(Consts K, LevelDev L,
         int ax = fc >> 1;
         float sg = (fc & 1) ? -1.0f : 1.0f;
         if (s.iarr[I_WALL + fc]) {
-          ee[ax] = fmaf(sg, s.VB[(2 * fc) * NP + o], ee[ax]);
+          ee[ax] = fmaf(sg, s.VB[(2 * fc) * VS + o], ee[ax]);
         } else {
-          float am = s.VB[(2 * fc) * NP + o], ap = s.VB[(2 * fc + 1) * NP + o];
+          float am = s.VB[(2 * fc) * VS + o], ap = s.VB[(2 * fc + 1) * VS + o];
           float w1 = s.sc[C_W + 3 * fc], w2 = s.sc[C_W + 3 * fc + 1], w3 = s.sc[C_W + 3 * fc + 2];
           d[ax] = fmaf(sg, fmaf(w1, am, w2 * ap), d[ax]);
           ee[ax] = fmaf(sg * w3, ap - am, ee[ax]);
