@@ -106,6 +106,80 @@ nrmg_status nrmg_learned_combine(const double *dev_prolonged, const float *dev_y
  * residual of the context.  Synchronizes. */
 nrmg_status nrmg_set_state_from_fields(nrmg_ctx *ctx, const double *dev_fields);
 
+/* ---- learned coarse-level correction of the lid-driven cavity family.
+ * The paper's cycle updates the fine grid with the coarse change carried over piecewise
+ * constant (eq. rewritten-update: f^ = f-_h - f-_H + f~_H in each fine cell of a coarse cell).
+ * This library adds, on the finest level only, a network's correction of that update: the
+ * network sees the coarse change of the ten learned fields (f~_H - f-_H) interpolated to the
+ * fine grid and the fine fields after the plain update, and predicts the remaining error of
+ * those ten fields.  Its correction is kept only when the residual norm of eq.
+ * (relative-residual) right after the update is smaller with it than without it; otherwise
+ * the plain update stands.  The converged solution is still R(f) = 0 of the paper's operator.
+ *
+ * Scaling: with s the largest |change| of the ten coarse fields times
+ * NRMG_CORR_FIELD_SCALE / U (over all coarse cells and fields), the network input is
+ * x [H*W][NRMG_CORR_CIN] FP32:
+ *   0..9   the interpolated coarse change (bilinear between cell centres, constant beyond
+ *          the outermost ones) times NRMG_CORR_FIELD_SCALE / (U s);
+ *   10..19 the fine fields after the plain update minus their rest values (1 for rho and
+ *          theta), times NRMG_CORR_FIELD_SCALE / U;
+ *   20..28 log10 Kn, log10 (Kn W / lx), U, x / lx, y / ly and the four wall indicators, as
+ *          channels 10..18 of nrmg_learned_features;
+ * and its output y [H*W][10] is the correction of the ten fields in units of U s /
+ * NRMG_CORR_FIELD_SCALE.  The correction enters each cell's Grad expansion as a linear
+ * increment (rho += d_rho; f_{e_i} += rho' d_u_i; every f_{2e_d} += rho' (3 d_theta + |d_u|^2) / 6
+ * with rho' = rho + d_rho; f_{e_i+e_j} += d_s_ij / (1 + delta_ij) with the trace of d_s removed;
+ * f_{3e_i} and f_{e_i+2e_d} += d_q_i / 5), after which the cell is projected back to Grad form
+ * as after a sweep update. */
+#define NRMG_CORR_CIN 29
+#define NRMG_CORR_FIELD_SCALE 10.0
+
+/* Device workspace of nrmg_fas_cycle_learned for this context (0 for a one-level context or
+ * an odd finest grid). */
+size_t nrmg_learned_cycle_workspace_bytes(const nrmg_ctx *ctx);
+
+/* Which residual decides whether the correction is kept: right after the update (both
+ * candidates before the post-smoothing), after the post-smoothing (each candidate smoothed
+ * s2 times; the cheaper test leaves high-frequency defects of a correction to the judge, which
+ * the smoother would remove), or none (the correction is always kept). */
+#define NRMG_JUDGE_UPDATE 0
+#define NRMG_JUDGE_SMOOTHED 1
+#define NRMG_JUDGE_NONE 2
+
+/* One cycle as nrmg_fas_cycle (Algorithm 2 on the finest level with gamma coarse cycles, then
+ * the mass correction), with a learned correction of the finest level's update:
+ *   net        the network (cin NRMG_CORR_CIN, cout 10, created on the context's stream, at
+ *              least H*W pixels), or NULL;
+ *   dev_y      used when net is NULL: a given correction [H*W][10] in the network's output
+ *              units (tests and bounds on what a correction can gain); NULL with net NULL =
+ *              the plain update (the cycle is then nrmg_fas_cycle's, bit for bit);
+ *   judge      NRMG_JUDGE_UPDATE, NRMG_JUDGE_SMOOTHED or NRMG_JUDGE_NONE;
+ *   Kn, U      the problem's Knudsen number and lid speed (the input scaling);
+ *   dev_ws     caller-owned device workspace, 256-byte aligned, ws_bytes >=
+ *              nrmg_learned_cycle_workspace_bytes;
+ *   dev_x_out, dev_fine_out  (may be NULL) receive the network input of this cycle and the
+ *              fine fields [H*W][14] after the plain update (training data);
+ *   scale_out  (host, may be NULL) receives s;
+ *   accepted_out (host, may be NULL) receives 1 when the network's correction was kept;
+ *   rel_res_out as for nrmg_fas_cycle.
+ * Synchronizes.  NRMG_ERR_ARG for a one-level context, a bad workspace or judge, or a network
+ * of the wrong shape or stream. */
+nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *dev_y, int judge, double Kn, double U,
+                                   void *dev_ws, size_t ws_bytes, float *dev_x_out, double *dev_fine_out,
+                                   double *scale_out, int *accepted_out, double *rel_res_out);
+
+/* The correction step alone, for tests and custom cycles: the finest level's state f becomes
+ * Grad(f + increment) with the increment above for the fields U scale y / NRMG_CORR_FIELD_SCALE
+ * (dev_y [cells][10] FP32 in the order rho, u1, u2, theta, s11, s12, s22, s33, q1, q2).  No
+ * acceptance test.  NRMG_ERR_NONPHYSICAL when a cell leaves rho > 0, theta > 0 (the level is
+ * then undefined).  Synchronizes. */
+nrmg_status nrmg_learned_correct(nrmg_ctx *ctx, const float *dev_y, double scale, double U);
+
+/* Training target of the correction: dev_t [cells][10] = (converged - fine) of the ten learned
+ * fields times NRMG_CORR_FIELD_SCALE / (U scale) (fields [cells][14] FP64 as nrmg_fields). */
+nrmg_status nrmg_learned_correction_targets(const double *dev_fine, const double *dev_converged, int cells, double U,
+                                            double scale, float *dev_t, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1147,6 +1147,151 @@ nrmg_status nrmg_fas_cycle(nrmg_ctx *ctx, double *rel_res_out) {
   return NRMG_OK;
 }
 
+// ------------------------------------------------------------------ learned coarse-level correction
+namespace {
+// Workspace of nrmg_fas_cycle_learned: coarse fields before and after the coarse cycles, fine
+// fields after the plain update, network input and output, the saved finest state, the scale.
+struct LearnWs {
+  double *cb, *ca, *fine, *bP, *bF, *btp, *cP, *cF, *ctp, *s;
+  float *x, *y;
+};
+size_t learned_ws(const nrmg_ctx *ctx, char *base, LearnWs *w) {
+  const LevelDev &Lf = ctx->lev[ctx->levels - 1], &Lc = ctx->lev[ctx->levels - 2];
+  Carver cv;
+  cv.base = base;
+  LearnWs t;
+  t.cb = cv.take<double>((size_t)Lc.ncell * 14);
+  t.ca = cv.take<double>((size_t)Lc.ncell * 14);
+  t.fine = cv.take<double>((size_t)Lf.ncell * 14);
+  t.x = cv.take<float>((size_t)Lf.ncell * NRMG_CORR_CIN);
+  t.y = cv.take<float>((size_t)Lf.ncell * NRMG_LEARN_COUT);
+  t.bP = cv.take<double>((size_t)Lf.ncell * 4);
+  t.bF = cv.take<double>((size_t)Lf.ncell * ctx->NP);
+  t.btp = cv.take<double>((size_t)Lf.ncell);
+  t.cP = cv.take<double>((size_t)Lf.ncell * 4);
+  t.cF = cv.take<double>((size_t)Lf.ncell * ctx->NP);
+  t.ctp = cv.take<double>((size_t)Lf.ncell);
+  t.s = cv.take<double>(8);
+  if (w) *w = t;
+  return cv.off;
+}
+}  // namespace
+
+size_t nrmg_learned_cycle_workspace_bytes(const nrmg_ctx *ctx) {
+  if (!ctx || ctx->levels < 2) return 0;
+  const LevelDev &Lf = ctx->lev[ctx->levels - 1], &Lc = ctx->lev[ctx->levels - 2];
+  if (Lc.nx * 2 != Lf.nx || Lc.ny * 2 != Lf.ny) return 0;
+  return learned_ws(ctx, nullptr, nullptr) + 256;
+}
+
+// copy of the finest level's state (params, coefficients, theta^(1-omega)) between the level and
+// a workspace slot
+static nrmg_status copy_state(nrmg_ctx *ctx, double *dP, double *dF, double *dtp, const double *sP, const double *sF,
+                              const double *stp) {
+  const LevelDev &Lf = ctx->lev[ctx->levels - 1];
+  CK(cudaMemcpyAsync(dP, sP, sizeof(double) * 4 * Lf.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(dF, sF, sizeof(double) * ctx->NP * Lf.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(dtp, stp, sizeof(double) * Lf.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *dev_y, int judge, double Kn, double U,
+                                   void *dev_ws, size_t ws_bytes, float *dev_x_out, double *dev_fine_out,
+                                   double *scale_out, int *accepted_out, double *rel_res_out) {
+  if (!ctx || !dev_ws || ((uintptr_t)dev_ws & 255) != 0 || !(Kn > 0.0) || !(U > 0.0)) return NRMG_ERR_ARG;
+  if (judge != NRMG_JUDGE_UPDATE && judge != NRMG_JUDGE_SMOOTHED && judge != NRMG_JUDGE_NONE) return NRMG_ERR_ARG;
+  const size_t need = nrmg_learned_cycle_workspace_bytes(ctx);
+  if (need == 0 || ws_bytes < need) return NRMG_ERR_ARG;
+  const int K = ctx->levels - 1;
+  LevelDev &Lf = ctx->lev[K], &Lc = ctx->lev[K - 1];
+  if (net && !net_fits(net, NRMG_CORR_CIN, NRMG_LEARN_COUT, (long long)Lf.ncell, ctx->stream)) return NRMG_ERR_ARG;
+  LearnWs w;
+  learned_ws(ctx, (char *)dev_ws, &w);
+  float *x = dev_x_out ? dev_x_out : w.x;
+  double *fine = dev_fine_out ? dev_fine_out : w.fine;
+  const nrmg_opts &o = ctx->opts;
+  cudaStream_t st = ctx->stream;
+  nrmg_status s;
+  Lf.has_r = 0;
+  if (!ctx->have_res0) {
+    if ((s = norm_of(ctx, K, nullptr, &ctx->res0)) != NRMG_OK) return s;
+    ctx->have_res0 = 1;
+  }
+  // Algorithm 2 on the finest level (as nmg), with the coarse change and the plain update open
+  if ((s = smooth_level(ctx, K, o.s1)) != NRMG_OK) return s;
+  if ((s = two_grid_setup(ctx, K)) != NRMG_OK) return s;
+  CK(launch_fields(ctx->K, Lc, w.cb, st));
+  for (int g = 0; g < o.gamma; ++g)
+    if ((s = nmg(ctx, K - 1)) != NRMG_OK) return s;
+  CK(launch_fields(ctx->K, Lc, w.ca, st));
+  if ((s = two_grid_update(ctx, K)) != NRMG_OK) return s;
+  CK(launch_fields(ctx->K, Lf, fine, st));
+  CK(launch_corr_inputs(w.cb, w.ca, Lc.ny, Lc.nx, fine, ctx->grid.lx, ctx->grid.ly, Kn, U, w.s, x, st));
+  ctx->launches += 5;
+  int accepted = 0;
+  bool smoothed = false;  // the level already holds the post-smoothed winner
+  if (net || dev_y) {
+    const float *y = dev_y;
+    if (net) {
+      if ((s = nrmg_net_forward(net, x, 1, Lf.ny, Lf.nx, w.y)) != NRMG_OK) return s;
+      y = w.y;
+    }
+    double r_plain = 0.0, r_net = 0.0;
+    if (judge == NRMG_JUDGE_UPDATE && (s = norm_of(ctx, K, nullptr, &r_plain)) != NRMG_OK) return s;
+    if ((s = copy_state(ctx, w.bP, w.bF, w.btp, Lf.P, Lf.F, Lf.tp)) != NRMG_OK) return s;  // the plain update
+    CK(launch_field_correct(ctx->K, Lf, y, w.s, U, grid_for(ctx, 3, Lf.ncell), st));
+    ctx->launches += 1;
+    bool physical = true;
+    if (judge == NRMG_JUDGE_UPDATE) {
+      s = norm_of(ctx, K, nullptr, &r_net);  // a non-physical candidate reports here (status cleared)
+      if (s != NRMG_OK && s != NRMG_ERR_NONPHYSICAL) return s;
+      physical = s == NRMG_OK;
+      accepted = physical && isfinite(r_net) && r_net < r_plain;
+    } else {
+      if ((s = sync_status(ctx)) != NRMG_OK && s != NRMG_ERR_NONPHYSICAL) return s;
+      physical = s == NRMG_OK;
+      accepted = physical;
+      if (physical && judge == NRMG_JUDGE_SMOOTHED) {
+        // smooth the candidate, keep it aside, smooth the plain update, compare
+        s = smooth_level(ctx, K, o.s2);
+        if (s == NRMG_OK) s = norm_of(ctx, K, nullptr, &r_net);
+        if (s != NRMG_OK && s != NRMG_ERR_NONPHYSICAL && s != NRMG_ERR_TIMEOUT) return s;
+        accepted = s == NRMG_OK && isfinite(r_net);
+        if (accepted && (s = copy_state(ctx, w.cP, w.cF, w.ctp, Lf.P, Lf.F, Lf.tp)) != NRMG_OK) return s;
+        if ((s = copy_state(ctx, Lf.P, Lf.F, Lf.tp, w.bP, w.bF, w.btp)) != NRMG_OK) return s;
+        if ((s = smooth_level(ctx, K, o.s2)) != NRMG_OK) return s;
+        if ((s = norm_of(ctx, K, nullptr, &r_plain)) != NRMG_OK) return s;
+        accepted = accepted && r_net < r_plain;
+        if (accepted && (s = copy_state(ctx, Lf.P, Lf.F, Lf.tp, w.cP, w.cF, w.ctp)) != NRMG_OK) return s;
+        smoothed = true;
+      }
+    }
+    if (!accepted && !smoothed && (s = copy_state(ctx, Lf.P, Lf.F, Lf.tp, w.bP, w.bF, w.btp)) != NRMG_OK) return s;
+  }
+  if (!smoothed && (s = smooth_level(ctx, K, o.s2)) != NRMG_OK) return s;
+  if ((s = mass_correct(ctx)) != NRMG_OK) return s;
+  double r = 0.0;
+  if ((s = norm_of(ctx, K, nullptr, &r)) != NRMG_OK) return s;
+  if (rel_res_out) *rel_res_out = ctx->res0 > 0.0 ? r / ctx->res0 : 0.0;
+  if (accepted_out) *accepted_out = accepted;
+  if (scale_out) {
+    CK(cudaMemcpyAsync(ctx->hpin, w.s, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *scale_out = ctx->hpin[0];
+  }
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_learned_correct(nrmg_ctx *ctx, const float *dev_y, double scale, double U) {
+  if (!ctx || !dev_y || !(scale > 0.0) || !(U > 0.0) || !isfinite(scale * U)) return NRMG_ERR_ARG;
+  LevelDev &Lf = ctx->lev[ctx->levels - 1];
+  ctx->hpin[0] = scale;
+  CK(cudaMemcpyAsync(ctx->dscal + 16, ctx->hpin, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(launch_field_correct(ctx->K, Lf, dev_y, ctx->dscal + 16, U, grid_for(ctx, 3, Lf.ncell), ctx->stream));
+  ctx->launches += 1;
+  return sync_status(ctx);
+}
+
 nrmg_status nrmg_solve(nrmg_ctx *ctx, double tol, int max_cycles, int *cycles_out, double *rel_res_out) {
   if (!ctx || !(tol >= 0.0) || max_cycles < 0) return NRMG_ERR_ARG;
   const int K = ctx->levels - 1;

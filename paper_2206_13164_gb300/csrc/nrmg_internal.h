@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct nrmg_net;
+
 namespace nrmg {
 
 constexpr int kMaxM = 16;
@@ -149,5 +151,19 @@ int occupancy_corr(int M, int NP);
 
 // 13-moment Grad state of given fields (nrmg_net.cu): P [ncell][4], F [ncell][NP] in graded order.
 cudaError_t launch_grad13(const double *fields, int ncell, int M, int NP, double *P, double *F, cudaStream_t st);
+
+// The network (nrmg_net.cu) has these input and output channel counts, room for `pixels`
+// pixels and runs on stream st.
+bool net_fits(const ::nrmg_net *net, int cin, int cout, long long pixels, cudaStream_t st);
+
+// Learned coarse-level correction (nrmg_net.cu): the scale s of the coarse change (device
+// scalar) and the network input x [4 Hc Wc][NRMG_CORR_CIN] on the finest grid.
+cudaError_t launch_corr_inputs(const double *coarse_before, const double *coarse_after, int Hc, int Wc,
+                               const double *fine_fields, double lx, double ly, double Kn, double U, double *s_dev,
+                               float *x, cudaStream_t st);
+// f <- Grad(f + the increment of the ten learned fields U s y / NRMG_CORR_FIELD_SCALE) on every cell
+// of L (nrmg_mixed.cu); y [ncell][10] FP32, s the device scalar above.
+cudaError_t launch_field_correct(const Consts &K, const LevelDev &L, const float *y, const double *s_dev, double U,
+                                 int grid, cudaStream_t st);
 
 }  // namespace nrmg

@@ -806,12 +806,67 @@ __global__ void __launch_bounds__(kThreads) mixed_update_kernel(Consts K, LevelD
   }
 }
 
+// ------------------------------------------------------------------ learned field correction
+// f <- Grad(f + increment) with the increment of the ten learned fields (rho, u1, u2, theta,
+// s11, s12, s22, s33, q1, q2) d = U s y / 10 written into the cell's own Grad expansion:
+// rho += d_rho; f_{e_i} += rho' d_u_i; every f_{2e_d} += rho' (3 d_theta + |d_u|^2) / 6 (the
+// temperature of the new velocity); f_{e_i+e_j} += d_s_ij / (1 + delta_ij) with the trace of d_s
+// removed; f_{3e_i} and f_{e_i+2e_d} += d_q_i / 5 (q_i = 2 f_{3e_i} + sum_d f_{e_i+2e_d}).
+__global__ void __launch_bounds__(kThreads) field_correct_kernel(Consts K, LevelDev L, const float *y, const double *sdev,
+                                                                 double U) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Sm s = bind_smem_f64(smem_raw, K.M, K.N, K.NP);
+  const int tid = threadIdx.x, N = K.N, NE = K.NE, NP = K.NP;
+  for (int e = tid; e < 3 * NE + N; e += kThreads) s.tslot[e] = K.tab_i32[e];
+  for (int e = tid; e < 13 * N + NE; e += kThreads) s.tmem[e] = K.tab_u16[e];
+  __syncthreads();
+  const int *iq = K.tab_i32 + K.iq_off, *is = iq + 12;  // heat-flux indices [3][4]; idx(e_i + e_j), i <= j
+  const double fac = U * sdev[0] / 10.0;
+  for (int c = blockIdx.x; c < L.ncell; c += gridDim.x) {
+    const float *yc = y + (size_t)c * 10;
+    double d[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) d[k] = fac * (double)yc[k];
+    const double rho1 = L.F[(size_t)c * NP] + d[0];
+    const double tr = (d[4] + d[6] + d[7]) * (1.0 / 3.0);
+    const double iso = rho1 * (3.0 * d[3] + d[1] * d[1] + d[2] * d[2]) * (1.0 / 6.0);
+    for (int q = tid; q < NE; q += kThreads) {
+      const int o = s.eidx[q];
+      double v = L.F[(size_t)c * NP + o];
+      if (o == 0) v += d[0];
+      if (o == K.idx_e[0]) v += rho1 * d[1];
+      if (o == K.idx_e[1]) v += rho1 * d[2];
+      if (o == K.idx_2e[0]) v += iso + 0.5 * (d[4] - tr);
+      if (o == K.idx_2e[1]) v += iso + 0.5 * (d[6] - tr);
+      if (o == K.idx_2e[2]) v += iso + 0.5 * (d[7] - tr);
+      if (o == is[1]) v += d[5];
+      for (int i = 0; i < 2; ++i)
+        for (int m = 0; m < 3; ++m)
+          if (o == iq[4 * i + 1 + m] && (m != i || o == iq[4 * i])) v += 0.2 * d[8 + i];
+      s.VA[o] = v;
+    }
+    __syncthreads();
+    double pc[4];
+    for (int e = 0; e < 4; ++e) pc[e] = L.P[(size_t)c * 4 + e];
+    bool ok = regrad_mixed(K, s, pc);
+    for (int q = tid; q < NE; q += kThreads) {
+      const int o = s.eidx[q];
+      L.F[(size_t)c * NP + o] = s.VB[o];
+    }
+    if (tid < 4) L.P[(size_t)c * 4 + tid] = s.sc[S_NEWP + tid];
+    if (tid == 4) L.tp[c] = s.sc[S_TPN];
+    if (!ok && tid == 0) atomicCAS(K.status, 0, kStNonPhysical);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 static void init_attrs_mixed() {
   static bool done = false;
   if (done) return;
   cudaFuncSetAttribute(fs_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(mixed_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(field_correct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   done = true;
 }
 
@@ -835,6 +890,14 @@ cudaError_t launch_mixed_update(const Consts &K, const LevelDev &L, int grid, cu
   init_attrs_mixed();
   size_t sm = make_layout(K.M, K.N, K.NP).total;
   mixed_update_kernel<<<grid, kThreads, sm, st>>>(K, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_correct(const Consts &K, const LevelDev &L, const float *y, const double *s_dev, double U,
+                                 int grid, cudaStream_t st) {
+  init_attrs_mixed();
+  size_t sm = make_layout(K.M, K.N, K.NP).total;
+  field_correct_kernel<<<grid, kThreads, sm, st>>>(K, L, y, s_dev, U);
   return cudaGetLastError();
 }
 

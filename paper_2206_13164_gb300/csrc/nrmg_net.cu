@@ -479,6 +479,72 @@ __global__ void combine_kernel(const double *__restrict__ pro, const float *__re
   }
 }
 
+// ---- learned coarse-level correction: scale of the coarse change, network input, targets
+constexpr double kCorrScale = NRMG_CORR_FIELD_SCALE;
+
+// s = max over coarse cells and learned fields of |after - before| kCorrScale / U (one block;
+// at least 1e-300 so that dividing by it stays finite)
+__global__ void corr_scale_kernel(const double *__restrict__ cb, const double *__restrict__ ca, int cells, double U,
+                                  double *__restrict__ s) {
+  __shared__ double red[1024];
+  double m = 0.0;
+  for (int q = threadIdx.x; q < cells * NRMG_LEARN_COUT; q += blockDim.x) {
+    const int c = q / NRMG_LEARN_COUT, k = q - c * NRMG_LEARN_COUT;
+    const size_t o = (size_t)c * 14 + c_learn_idx[k];
+    m = fmax(m, fabs(ca[o] - cb[o]));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s[0] = fmax(red[0] * kCorrScale / U, 1e-300);
+}
+
+__global__ void corr_features_kernel(const double *__restrict__ cb, const double *__restrict__ ca, int Hc, int Wc,
+                                     const double *__restrict__ fine, double lx, double ly, double Kn, double U,
+                                     const double *__restrict__ sdev, float *__restrict__ x) {
+  const int H = 2 * Hc, W = 2 * Wc;
+  const double inv_u = kCorrScale / U, inv_us = kCorrScale / (U * sdev[0]);
+  const float lkn = (float)log10(Kn), lkw = (float)log10(Kn * W / lx);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < H * W; c += gridDim.x * blockDim.x) {
+    const int I = c / W, J = c - I * W;
+    const int i = I >> 1, j = J >> 1;
+    const int in = (I & 1) ? min(i + 1, Hc - 1) : max(i - 1, 0);
+    const int jn = (J & 1) ? min(j + 1, Wc - 1) : max(j - 1, 0);
+    const size_t c00 = (size_t)(i * Wc + j) * 14, c01 = (size_t)(i * Wc + jn) * 14;
+    const size_t c10 = (size_t)(in * Wc + j) * 14, c11 = (size_t)(in * Wc + jn) * 14;
+    float *xc = x + (size_t)c * NRMG_CORR_CIN;
+    for (int k = 0; k < NRMG_LEARN_COUT; ++k) {
+      const int f = c_learn_idx[k];
+      const double d = 0.5625 * (ca[c00 + f] - cb[c00 + f]) + 0.1875 * ((ca[c01 + f] - cb[c01 + f]) +
+                                                                        (ca[c10 + f] - cb[c10 + f])) +
+                       0.0625 * (ca[c11 + f] - cb[c11 + f]);
+      xc[k] = (float)(d * inv_us);
+      xc[10 + k] = (float)((fine[(size_t)c * 14 + f] - c_learn_rest[k]) * inv_u);
+    }
+    xc[20] = lkn;
+    xc[21] = lkw;
+    xc[22] = (float)U;
+    xc[23] = (float)((J + 0.5) / W);
+    xc[24] = (float)((I + 0.5) / H);
+    xc[25] = I == 0 ? 1.f : 0.f;
+    xc[26] = J == W - 1 ? 1.f : 0.f;
+    xc[27] = I == H - 1 ? 1.f : 0.f;
+    xc[28] = J == 0 ? 1.f : 0.f;
+  }
+}
+
+__global__ void corr_targets_kernel(const double *__restrict__ fine, const double *__restrict__ conv, int cells,
+                                    double U, double scale, float *__restrict__ t) {
+  const double f = kCorrScale / (U * scale);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cells * NRMG_LEARN_COUT; q += gridDim.x * blockDim.x) {
+    const int c = q / NRMG_LEARN_COUT, k = q - c * NRMG_LEARN_COUT;
+    t[q] = (float)((conv[(size_t)c * 14 + c_learn_idx[k]] - fine[(size_t)c * 14 + c_learn_idx[k]]) * f);
+  }
+}
+
 // Graded positions of the Grad-13 coefficients (-1 when the degree exceeds M).
 struct GradIdx {
   int s[3][3];     // e_i + e_j
@@ -527,6 +593,13 @@ int grid_1d(long long work, int cap = 4096) {
 }  // namespace
 
 namespace nrmg {
+cudaError_t launch_corr_inputs(const double *cb, const double *ca, int Hc, int Wc, const double *fine, double lx,
+                               double ly, double Kn, double U, double *s_dev, float *x, cudaStream_t st) {
+  corr_scale_kernel<<<1, 1024, 0, st>>>(cb, ca, Hc * Wc, U, s_dev);
+  corr_features_kernel<<<grid_1d(4ll * Hc * Wc), 256, 0, st>>>(cb, ca, Hc, Wc, fine, lx, ly, Kn, U, s_dev, x);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_grad13(const double *fields, int ncell, int M, int NP, double *P, double *F, cudaStream_t st) {
   GradIdx gi;
   for (int i = 0; i < 3; ++i)
@@ -770,6 +843,12 @@ nrmg_status refresh_bf16(nrmg_net *n) {
 
 }  // namespace
 
+namespace nrmg {
+bool net_fits(const ::nrmg_net *n, int cin, int cout, long long pixels, cudaStream_t st) {
+  return n && n->cin == cin && n->cout == cout && pixels <= n->max_pixels && n->stream == st;
+}
+}  // namespace nrmg
+
 extern "C" {
 
 size_t nrmg_net_workspace_bytes(int cin, int hidden, int cout, long long max_pixels) {
@@ -881,6 +960,15 @@ nrmg_status nrmg_learned_features(const double *cf, int Hc, int Wc, double lx, d
 nrmg_status nrmg_learned_targets(const double *pro, const double *fine, int cells, double U, float *t, void *stream) {
   if (!pro || !fine || !t || cells < 1 || cells > (1 << 26) || !(U > 0.0)) return NRMG_ERR_ARG;
   targets_kernel<<<grid_1d((long long)cells * NRMG_LEARN_COUT), 256, 0, (cudaStream_t)stream>>>(pro, fine, cells, U, t);
+  NCK(cudaGetLastError());
+  return NRMG_OK;
+}
+
+nrmg_status nrmg_learned_correction_targets(const double *fine, const double *conv, int cells, double U,
+                                            double scale, float *t, void *stream) {
+  if (!fine || !conv || !t || cells < 1 || cells > (1 << 26) || !(U > 0.0) || !(scale > 0.0)) return NRMG_ERR_ARG;
+  corr_targets_kernel<<<grid_1d((long long)cells * NRMG_LEARN_COUT), 256, 0, (cudaStream_t)stream>>>(fine, conv, cells,
+                                                                                                    U, scale, t);
   NCK(cudaGetLastError());
   return NRMG_OK;
 }

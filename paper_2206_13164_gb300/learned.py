@@ -34,8 +34,11 @@ from . import nrmg
 from .nrmg import Batch, NrmgError, Solver
 
 CIN, COUT = 19, 10          # NRMG_LEARN_CIN, NRMG_LEARN_COUT
+CORR_CIN = 29               # NRMG_CORR_CIN
+JUDGE_UPDATE, JUDGE_SMOOTHED, JUDGE_NONE = 0, 1, 2  # NRMG_JUDGE_*
 HIDDEN = 64
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "lid_net.npz")
+CORR_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "corr_net.npz")
 
 _ready = False
 
@@ -71,6 +74,17 @@ def _lib():
         L.nrmg_learned_targets.argtypes = [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]
         L.nrmg_learned_combine.restype = c_int
         L.nrmg_learned_combine.argtypes = [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]
+        L.nrmg_learned_cycle_workspace_bytes.restype = c_size_t
+        L.nrmg_learned_cycle_workspace_bytes.argtypes = [c_void_p]
+        L.nrmg_fas_cycle_learned.restype = c_int
+        L.nrmg_fas_cycle_learned.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_void_p,
+                                             c_size_t, c_void_p, c_void_p, POINTER(c_double), POINTER(c_int),
+                                             POINTER(c_double)]
+        L.nrmg_learned_correct.restype = c_int
+        L.nrmg_learned_correct.argtypes = [c_void_p, c_void_p, c_double, c_double]
+        L.nrmg_learned_correction_targets.restype = c_int
+        L.nrmg_learned_correction_targets.argtypes = [c_void_p, c_void_p, c_int, c_double, c_double, c_void_p,
+                                                      c_void_p]
         _ready = True
     return L
 
@@ -193,6 +207,128 @@ def combine(prolonged: torch.Tensor, y: torch.Tensor, U: float) -> torch.Tensor:
     out = torch.empty_like(prolonged)
     _check(_lib().nrmg_learned_combine(_p(prolonged, torch.float64), _p(y.contiguous(), torch.float32), H * W, U,
                                        _p(out, torch.float64), _stream()), "nrmg_learned_combine")
+    return out
+
+
+# ---------------------------------------------------------------- learned coarse-level correction
+class LearnedCycle:
+    """FAS cycles of one solver with the learned correction of the finest level's update
+    (``nrmg_fas_cycle_learned``): the network's correction of the coarse change is kept only
+    when it lowers the residual norm right after the update.  net=None runs the plain cycle
+    (and still forms the network input, for training data)."""
+
+    def __init__(self, solver: Solver, Kn: float, U: float, judge: int = JUDGE_UPDATE):
+        self.s, self.Kn, self.U, self.judge = solver, Kn, U, judge
+        self.L = _lib()
+        nbytes = self.L.nrmg_learned_cycle_workspace_bytes(solver.ctx)
+        if nbytes == 0:
+            raise NrmgError(nrmg.ERR_ARG, "nrmg_learned_cycle_workspace_bytes")
+        self.nbytes = nbytes
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=solver.device)
+        self.accepted = 0
+        self.cycles = 0
+
+    def cycle(self, net=None, x_out=None, fine_out=None, y=None, judge=None):
+        """One cycle: (relative residual, correction kept, scale s of the coarse change).
+        y: a given correction [H, W, 10] (network units) when net is None."""
+        rel, acc, sc = c_double(0.0), c_int(0), c_double(0.0)
+        judge = self.judge if judge is None else judge
+        st = self.L.nrmg_fas_cycle_learned(self.s.ctx, net.h if net is not None else None,
+                                           _p(y.contiguous(), torch.float32) if y is not None else None, judge,
+                                           self.Kn, self.U, c_void_p(self.ws.data_ptr()), self.nbytes,
+                                           _p(x_out, torch.float32) if x_out is not None else None,
+                                           _p(fine_out, torch.float64) if fine_out is not None else None,
+                                           ctypes.byref(sc), ctypes.byref(acc), ctypes.byref(rel))
+        _check(st, "nrmg_fas_cycle_learned")
+        self.cycles += 1
+        self.accepted += acc.value
+        return rel.value, bool(acc.value), sc.value
+
+    def solve(self, net=None, tol=1e-8, max_cycles=400):
+        """Cycles until the relative residual (of the solver's reference) is at most tol:
+        (cycles, relative residual, corrections kept)."""
+        rel, n0, a0 = 1.0, self.cycles, self.accepted
+        while self.cycles - n0 < max_cycles:
+            rel = self.cycle(net)[0]
+            if rel <= tol:
+                break
+        return self.cycles - n0, rel, self.accepted - a0
+
+
+def learned_correct(solver: Solver, y: torch.Tensor, scale: float, U: float):
+    """The correction step alone on the solver's finest level (``nrmg_learned_correct``):
+    y [cells, 10] float32 in network units."""
+    _check(_lib().nrmg_learned_correct(solver.ctx, _p(y.contiguous(), torch.float32), scale, U),
+           "nrmg_learned_correct")
+
+
+def correction_targets(fine: torch.Tensor, converged: torch.Tensor, U: float, scale: float) -> torch.Tensor:
+    """(converged - fine) of the ten learned fields in the units of the correction network."""
+    H, W, _ = fine.shape
+    t = torch.empty((H, W, COUT), dtype=torch.float32, device="cuda")
+    _check(_lib().nrmg_learned_correction_targets(_p(fine.contiguous(), torch.float64),
+                                                  _p(converged.contiguous(), torch.float64), H * W, U, scale,
+                                                  _p(t, torch.float32), _stream()), "nrmg_learned_correction_targets")
+    return t
+
+
+def correction_pairs(problems, N, M, ref_tol=1e-10, stop=1e-7, max_cycles=60, log=print):
+    """Training pairs of the correction network on the N x N cavity: for every (Kn, U), the
+    converged solution (batched plain solve to ref_tol), then the plain cycles from the
+    Maxwellian start; each cycle gives (network input, (converged - fine after the plain
+    update) in network units) until the relative residual reaches `stop`."""
+    t0 = time.perf_counter()
+    sol = [lid_solver(N, M, kn, u) for kn, u in problems]
+    b = Batch(sol)
+    b.solve(ref_tol, 400)
+    conv = [s.fields().clone() for s in sol]
+    b.close()
+    for s in sol:
+        s.close()
+    log(f"  {len(problems)} references on {N}x{N} in {time.perf_counter() - t0:.1f} s")
+    xs, ts = [], []
+    t0 = time.perf_counter()
+    for (kn, u), F in zip(problems, conv):
+        s = lid_solver(N, M, kn, u)
+        lc = LearnedCycle(s, kn, u)
+        for _ in range(max_cycles):
+            x = torch.empty((N, N, CORR_CIN), dtype=torch.float32, device="cuda")
+            fine = torch.empty((N, N, 14), dtype=torch.float64, device="cuda")
+            rel, _, sc = lc.cycle(None, x_out=x, fine_out=fine)
+            xs.append(x)
+            ts.append(correction_targets(fine, F, u, sc))
+            if rel <= stop:
+                break
+        s.close()
+    log(f"  {len(xs)} pairs in {time.perf_counter() - t0:.1f} s")
+    return torch.stack(xs), torch.stack(ts)
+
+
+def evaluate_correction(N, M, Kn, U, net, tol=1e-8, max_cycles=400, grid=0, judges=(JUDGE_UPDATE,)):
+    """Cycles and wall time to tol from the Maxwellian start: the plain cycle and the cycle
+    with the learned correction under each judge (\"learned\" for the first, \"learned_j<k>\"
+    for the others), and each learned solution's largest field difference from the plain one."""
+    out = {"N": N, "M": M, "Kn": Kn, "U": U}
+    runs = {}
+    names = [("plain", None, JUDGE_UPDATE)] + [("learned" if k == 0 else f"learned_j{j}", net, j)
+                                               for k, j in enumerate(judges)]
+    for name, nn, j in names:
+        s = lid_solver(N, M, Kn, U)
+        s.set_grid(grid)
+        lc = LearnedCycle(s, Kn, U, judge=j)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cyc, rel, acc = lc.solve(nn, tol, max_cycles)
+        torch.cuda.synchronize()
+        runs[name] = s
+        out[name] = {"cycles": cyc, "rel_res": rel, "kept": acc, "judge": j, "seconds": time.perf_counter() - t0}
+    fp = runs["plain"].fields()
+    for name, s in runs.items():
+        if name != "plain":
+            out[name]["field_rel_err"] = field_rel_errors(s.fields(), fp)
+    out["field_rel_err"] = out["learned"]["field_rel_err"]
+    for s in runs.values():
+        s.close()
     return out
 
 
@@ -469,6 +605,15 @@ def main(argv=None):
     ev.add_argument("--polish", type=int, default=2)
     ev.add_argument("--decide", type=int, default=2)
     ev.add_argument("--weights", default=WEIGHTS)
+    tc = sub.add_parser("train-correction", help="generate cycle data and train the coarse-correction network")
+    tc.add_argument("--n", type=int, default=64, help="training cavities")
+    tc.add_argument("--N", type=int, default=64)
+    tc.add_argument("--M", type=int, default=8)
+    tc.add_argument("--epochs", type=int, default=40)
+    tc.add_argument("--seed", type=int, default=2207)
+    tc.add_argument("--holdout", type=float, nargs=2, default=(0.03, 0.35), metavar=("KN", "U"))
+    tc.add_argument("--eval-N", type=int, default=128)
+    tc.add_argument("--out", default=CORR_WEIGHTS)
     pr = sub.add_parser("profile", help="a few forward passes and training steps on one image (profiling case)")
     pr.add_argument("--N", type=int, default=512)
     pr.add_argument("--reps", type=int, default=3)
@@ -482,6 +627,26 @@ def main(argv=None):
             net.train_step(x, t, 1e-4)
         torch.cuda.synchronize()
         print(f"profile case: {a.reps} forward passes and training steps on {a.N}x{a.N}", flush=True)
+        return
+    if a.cmd == "train-correction":
+        rng = np.random.default_rng(a.seed)
+        probs = draw_problems(a.n, rng, holdout=a.holdout)
+        t0 = time.perf_counter()
+        X, T = correction_pairs(probs, a.N, a.M)
+        t_data = time.perf_counter() - t0
+        net = Net(cin=CORR_CIN, cout=COUT, max_pixels=16 * a.N * a.N, seed=a.seed)
+        t0 = time.perf_counter()
+        hist = train(net, [(X, T)], a.epochs)
+        t_train = time.perf_counter() - t0
+        net.save(a.out, n_pairs=[int(X.shape[0])], sizes=[a.N], M=a.M, epochs=a.epochs, seed=a.seed,
+                 holdout=list(a.holdout), loss_history=hist, t_data_s=t_data, t_train_s=t_train, problems=a.n)
+        print(f"saved {a.out}: {X.shape[0]} pairs, final loss {hist[-1]:.4e}, data {t_data:.0f} s, "
+              f"training {t_train:.0f} s", flush=True)
+        del X, T
+        ev = evaluate_correction(a.eval_N, a.M, a.holdout[0], a.holdout[1],
+                                 Net.load(a.out, max_pixels=a.eval_N * a.eval_N),
+                                 judges=(JUDGE_UPDATE, JUDGE_SMOOTHED, JUDGE_NONE))
+        print(json.dumps(ev), flush=True)
         return
     if a.cmd == "eval":
         print(json.dumps(evaluate(a.N, a.M, a.Kn, a.U, Net.load(a.weights, max_pixels=a.N * a.N), start=a.start,

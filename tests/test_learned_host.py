@@ -49,3 +49,27 @@ def test_committed_weights_describe_their_training():
 
     assert z["params"].size == net_ref.n_params(learned.CIN, 64, learned.COUT)
     assert np.all(np.isfinite(z["params"]))
+
+
+def test_committed_correction_weights_describe_their_training():
+    import json
+    import os
+
+    assert os.path.exists(learned.CORR_WEIGHTS)
+    z = np.load(learned.CORR_WEIGHTS)
+    meta = json.loads(str(z["meta"]))
+    assert int(z["cin"]) == learned.CORR_CIN and int(z["cout"]) == learned.COUT and int(z["hidden"]) == 64
+    assert meta["sizes"] == [64] and meta["M"] == 8 and meta["holdout"] == [0.03, 0.35]
+    assert meta["n_pairs"][0] > meta["problems"]  # several cycles of every training cavity
+    from oracle import net_ref
+
+    assert z["params"].size == net_ref.n_params(learned.CORR_CIN, 64, learned.COUT)
+    assert np.all(np.isfinite(z["params"]))
+    # training lowered the loss
+    assert meta["loss_history"][-1] < 0.2 * meta["loss_history"][0]
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the behaviour without a GPU")
+def test_learned_cycle_refuses_to_run_without_cuda():
+    with pytest.raises(RuntimeError):
+        learned.lid_solver(16, 5, 0.1, 0.2)
