@@ -630,9 +630,14 @@ nrmg_status norm_of(nrmg_ctx *ctx, int level, double *out_dev_R, double *norm_ho
 nrmg_status two_grid_setup(nrmg_ctx *ctx, int lf) {
   nrmg_status s = residual(ctx, lf, kResDefect, nullptr, 0, nullptr);
   if (s != NRMG_OK) return s;
-  int g = grid_for(ctx, 2, ctx->lev[lf - 1].ncell);
-  CK(launch_restrict(ctx->K, ctx->lev[lf], ctx->lev[lf - 1], g, ctx->stream));
+  LevelDev &Lc = ctx->lev[lf - 1];
+  int g = grid_for(ctx, 2, Lc.ncell);
+  CK(launch_restrict(ctx->K, ctx->lev[lf], Lc, g, ctx->stream));
   ctx->launches += 1;
+  // the restricted defect is the coarse state's defect r_H - R_H(f_H): kept for the mixed
+  // smoother's first coarse smoothing (it has no other use on a coarse level)
+  if (ctx->opts.precision == 1)
+    CK(cudaMemcpyAsync(Lc.D, Lc.rF, sizeof(double) * ctx->NP * Lc.ncell, cudaMemcpyDeviceToDevice, ctx->stream));
   s = residual(ctx, lf - 1, kResCoarseRhs, nullptr, 0, nullptr);
   if (s != NRMG_OK) return s;
   ctx->lev[lf - 1].has_r = 1;
@@ -649,11 +654,13 @@ nrmg_status two_grid_update(nrmg_ctx *ctx, int lf) {
 // Mixed-precision smoothing of level `level`: FP64 defect d = r - R(f), `steps` FP32 sweeps of
 // the linearized correction equation L e = d (same cell order as Algorithm 1), then
 // f <- Grad(f + e) in FP64.
-nrmg_status smooth_mixed(nrmg_ctx *ctx, int level, int steps) {
+// defect_ready: L.D already holds r - R(f) of the current state (the restricted defect of a
+// level that two_grid_setup has just formed).
+nrmg_status smooth_mixed(nrmg_ctx *ctx, int level, int steps, bool defect_ready = false) {
   if (steps <= 0) return NRMG_OK;
   LevelDev &L = ctx->lev[level];
-  nrmg_status s = residual(ctx, level, kResDefect, nullptr, 0, nullptr);
-  if (s != NRMG_OK) return s;
+  nrmg_status s;
+  if (!defect_ready && (s = residual(ctx, level, kResDefect, nullptr, 0, nullptr)) != NRMG_OK) return s;
   CK(launch_mixed_prep(ctx->K, L, ctx->stream));  // also sets every correction word to version 0
   CK(cudaMemsetAsync(ctx->K.queue, 0, sizeof(int), ctx->stream));
   const int *queue = nullptr;
@@ -679,20 +686,23 @@ nrmg_status smooth_mixed(nrmg_ctx *ctx, int level, int steps) {
   return NRMG_OK;
 }
 
-nrmg_status smooth_level(nrmg_ctx *ctx, int level, int steps) {
-  if (ctx->opts.precision == 1 && !ctx->mixed_off && level > 0) return smooth_mixed(ctx, level, steps);
+nrmg_status smooth_level(nrmg_ctx *ctx, int level, int steps, bool defect_ready = false) {
+  if (ctx->opts.precision == 1 && !ctx->mixed_off && level > 0) return smooth_mixed(ctx, level, steps, defect_ready);
   return smooth(ctx, level, steps);
 }
 
 // Algorithm 2 on level k
-nrmg_status nmg(nrmg_ctx *ctx, int k) {
+// first_visit: the coarse level has just been formed by two_grid_setup, so its defect r - R(f)
+// is the restricted defect that two_grid_setup left in L.D (the mixed smoother then skips its
+// own defect evaluation).
+nrmg_status nmg(nrmg_ctx *ctx, int k, bool first_visit = false) {
   const nrmg_opts &o = ctx->opts;
   nrmg_status s;
   if (k == 0) return smooth(ctx, 0, o.s3);
-  if ((s = smooth_level(ctx, k, o.s1)) != NRMG_OK) return s;
+  if ((s = smooth_level(ctx, k, o.s1, first_visit)) != NRMG_OK) return s;
   if ((s = two_grid_setup(ctx, k)) != NRMG_OK) return s;
   for (int g = 0; g < o.gamma; ++g)
-    if ((s = nmg(ctx, k - 1)) != NRMG_OK) return s;
+    if ((s = nmg(ctx, k - 1, g == 0)) != NRMG_OK) return s;
   if ((s = two_grid_update(ctx, k)) != NRMG_OK) return s;
   return smooth_level(ctx, k, o.s2);
 }
@@ -1222,7 +1232,7 @@ nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *de
   if ((s = two_grid_setup(ctx, K)) != NRMG_OK) return s;
   CK(launch_fields(ctx->K, Lc, w.cb, st));
   for (int g = 0; g < o.gamma; ++g)
-    if ((s = nmg(ctx, K - 1)) != NRMG_OK) return s;
+    if ((s = nmg(ctx, K - 1, g == 0)) != NRMG_OK) return s;
   CK(launch_fields(ctx->K, Lc, w.ca, st));
   if ((s = two_grid_update(ctx, K)) != NRMG_OK) return s;
   CK(launch_fields(ctx->K, Lf, fine, st));

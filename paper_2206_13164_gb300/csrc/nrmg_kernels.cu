@@ -147,10 +147,10 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
   //   items 2..5: E -> slot 1, W -> slot 2, N -> slot 5, S -> slot 6
   const int NE = K.NE;
   // one slope item element: writes the face state(s) it feeds
-  auto face_item = [&](int q) {
-    const int kk = q / (4 + NE);
-    int it = part_item(kPart, kk), e = q - kk * (4 + NE);
-    if (e >= 4) e = 4 + s.eidx[e - 4];
+  // one slope item element (item kk of the part, column e of the stencil rows: 0..3 the
+  // params, 4 + o coefficient o): writes the face state(s) it feeds
+  auto face_item = [&](int kk, int e) {
+    const int it = part_item(kPart, kk);
     int X = c_it_x[it], Xm = c_it_m[it], Xp = c_it_p[it];
     if (!s.iarr[I_EX + X]) return;
     bool on = K.reach == 2 && K.slope != 0 && s.iarr[I_EX + Xm] && s.iarr[I_EX + Xp];
@@ -192,84 +192,125 @@ __device__ inline void cell_residual(const Consts &K, const LevelDev &L, Sm &s, 
       if (v1 >= 0) s.VA[v1 * NP + e - 4] = x1;
     }
   };
-  {
-    const int tot = part_items(kPart) * (4 + NE);
-    for (int q = tid; q < tot; q += 2 * kThreads) {
-      face_item(q);
-      if (q + kThreads < tot) face_item(q + kThreads);
+  // The coefficient elements of the face states (the FP64-heavy part) run on every warp but the
+  // last; the last warp meanwhile runs the short dependent chains that the transforms wait for:
+  // the face states' basis params, the destination bases, the time step and collision
+  // frequency, the HLL weights and the coefficients of the transform series.
+  constexpr int kCoefThreads = kThreads - 32;
+  if (tid < kCoefThreads) {
+    const int tot = part_items(kPart) * NE;
+    for (int q = tid; q < tot; q += 2 * kCoefThreads) {
+      const int k0 = q / NE;
+      face_item(k0, 4 + s.eidx[q - k0 * NE]);
+      const int q1 = q + kCoefThreads;
+      if (q1 < tot) {
+        const int k1 = q1 / NE;
+        face_item(k1, 4 + s.eidx[q1 - k1 * NE]);
+      }
+    }
+    if (!kCoherent && tid == 64) {  // theta^-k of the norm weights (the residual kernel's norm)
+      double it = 1.0 / pc[3], t = 1.0;
+      for (int k = 0; k <= K.M; ++k) {
+        s.sc[S_TPOW + k] = t;
+        t *= it;
+      }
+    }
+    if (tid >= 96 && tid < 99 && K.model == 1) {
+      // q_i = 2 f_{3e_i} + sum_d f_{2e_d + e_i} (eq. moments-relation)
+      int ii = tid - 96;
+      const double *f = pc + 4;
+      const int *iq = K.tab_i32 + K.iq_off + 4 * ii;
+      double q = 2.0 * f[iq[0]];
+      for (int d = 0; d < 3; ++d) q += f[iq[1 + d]];
+      s.sc[S_Q + ii] = q;
+    }
+    if (kES) es_factors(K.tab_i32 + K.iq_off + 12, K.Pr, K.M, pc + 4, s.sc);
+  } else {
+    const int lane = tid - kCoefThreads;
+    if (lane < part_items(kPart) * 4) face_item(lane >> 2, lane & 3);
+    // destination bases: the cell, or the wall for a wall face's slot 2f
+    for (int t = lane; t < 4 * kNV; t += 32) {
+      int v = t >> 2, e = t & 3;
+      int f = v >> 1;
+      if (v < 8 && s.iarr[I_WALL + f] && !(v & 1)) {
+        int w = c_face_wall[f];
+        s.vdst[v * 4 + e] = e < 3 ? K.wall_u[w][e] : K.wall_theta[w];
+      } else {
+        s.vdst[v * 4 + e] = pc[e];
+      }
+    }
+    if (lane == 0) {
+      int na = 0;
+      for (int f = 0; f < 4; ++f) {
+        if (!part_has_face(kPart, f)) continue;
+        s.iarr[I_ACT + na++] = 2 * f;
+        if (!s.iarr[I_WALL + f]) s.iarr[I_ACT + na++] = 2 * f + 1;
+      }
+      if (L.has_r && kPart != 1) s.iarr[I_ACT + na++] = 8;
+      s.iarr[I_NACT] = na;
+    }
+    __syncwarp();
+    // lanes 0..3: HLL weights of interior face `lane`, F = w1 Xi a- + w2 Xi a+ + w3 (a+ - a-);
+    // lane 4: the local time step (eq. local-CFL) and the collision frequency.  One code path:
+    // two square roots, one reciprocal.
+    if (lane < 5) {
+      const int f = lane & 3, ax = f >> 1;
+      const bool hll = lane < 4;
+      const double *pm = hll ? s.vsrc + (2 * f) * 4 : pc, *pp = hll ? s.vsrc + (2 * f + 1) * 4 : pc;
+      const double sm = sqrt(pm[3]), sp = sqrt(pp[3]);
+      double sL = fmin(pm[ax] - K.C * sm, pp[ax] - K.C * sp);
+      double sR = fmax(pm[ax] + K.C * sm, pp[ax] + K.C * sp);
+      double den = sR - sL;
+      if (!hll) den = (fabs(pc[0]) + K.C * sm) * inv_hx(L, i) + (fabs(pc[1]) + K.C * sm) * inv_hy(L, j);
+      const double inv = 1.0 / den;
+      if (hll) {
+        if (!s.iarr[I_WALL + f] && part_has_face(kPart, f)) {
+          double w1, w2, w3;
+          if (sL >= 0.0) {
+            w1 = 1.0; w2 = 0.0; w3 = 0.0;
+          } else if (sR <= 0.0) {
+            w1 = 0.0; w2 = 1.0; w3 = 0.0;
+          } else {
+            w1 = sR * inv; w2 = -sL * inv; w3 = sL * sR * inv;
+          }
+          s.sc[S_W + 3 * f] = w1;
+          s.sc[S_W + 3 * f + 1] = w2;
+          s.sc[S_W + 3 * f + 2] = w3;
+        }
+      } else {
+        const double tpc = kCoherent ? __ldcg(L.tp + c) : L.tp[c];
+        const double nu = K.nu0 * pc[4] * tpc;
+        s.sc[S_NU] = nu;
+        double dt = K.cfl * inv;
+        if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / nu);
+        s.sc[S_DT] = dt;
+      }
+    }
+    __syncwarp();
+    // series coefficients of every active vector and direction (setup_coeffs on this warp)
+    {
+      const int M = K.M, na = s.iarr[I_NACT];
+      for (int t = lane; t < na * 3; t += 32) {
+        int v = s.iarr[I_ACT + t / 3], d = t % 3;
+        double a = s.vdst[v * 4 + d] - s.vsrc[v * 4 + d];
+        double b = 0.5 * (s.vdst[v * 4 + 3] - s.vsrc[v * 4 + 3]);
+        double *cf = s.cf + (v * 3 + d) * (M + 1);
+        double cm = 1.0, ck = -a;
+        cf[0] = cm;
+        cf[1] = ck;
+#pragma unroll
+        for (int k = 1; k < kMaxM; ++k) {
+          if (k >= M) break;
+          double u = (-2.0 * b * cinv(0.0, k)) * cm;
+          double cn = fma(-a * cinv(0.0, k), ck, u);
+          cf[k + 1] = cn;
+          cm = ck;
+          ck = cn;
+        }
+        s.vflag[v * 3 + d] = ((a == 0.0 && b == 0.0) ? 1 : 0) | (a == 0.0 ? 2 : 0);
+      }
     }
   }
-  // destination bases: the cell, or the wall for a wall face's slot 2f
-  if (tid < 4 * kNV) {
-    int v = tid >> 2, e = tid & 3;
-    int f = v >> 1;
-    if (v < 8 && s.iarr[I_WALL + f] && !(v & 1)) {
-      int w = c_face_wall[f];
-      s.vdst[v * 4 + e] = e < 3 ? K.wall_u[w][e] : K.wall_theta[w];
-    } else {
-      s.vdst[v * 4 + e] = pc[e];
-    }
-  }
-  if (tid == 0) {
-    int na = 0;
-    for (int f = 0; f < 4; ++f) {
-      if (!part_has_face(kPart, f)) continue;
-      s.iarr[I_ACT + na++] = 2 * f;
-      if (!s.iarr[I_WALL + f]) s.iarr[I_ACT + na++] = 2 * f + 1;
-    }
-    if (L.has_r && kPart != 1) s.iarr[I_ACT + na++] = 8;
-    s.iarr[I_NACT] = na;
-  }
-  if (tid == 32) {
-    const double *f = pc + 4;
-    double rho = f[0], th = pc[3];
-    const double tpc = kCoherent ? __ldcg(L.tp + c) : L.tp[c];
-    const double nu = K.nu0 * rho * tpc;
-    s.sc[S_NU] = nu;
-    double sq = sqrt(th);
-    double dt = K.cfl / ((fabs(pc[0]) + K.C * sq) * inv_hx(L, i) + (fabs(pc[1]) + K.C * sq) * inv_hy(L, j));
-    if (K.dtnu > 0.0) dt = fmin(dt, K.dtnu / nu);
-    s.sc[S_DT] = dt;
-  }
-  if (tid == 64) {
-    double it = 1.0 / pc[3], t = 1.0;
-    for (int k = 0; k <= K.M; ++k) {
-      s.sc[S_TPOW + k] = t;
-      t *= it;
-    }
-  }
-  if (tid >= 96 && tid < 99 && K.model == 1) {
-    // q_i = 2 f_{3e_i} + sum_d f_{2e_d + e_i} (eq. moments-relation)
-    int ii = tid - 96;
-    const double *f = pc + 4;
-    const int *iq = K.tab_i32 + K.iq_off + 4 * ii;
-    double q = 2.0 * f[iq[0]];
-    for (int d = 0; d < 3; ++d) q += f[iq[1 + d]];
-    s.sc[S_Q + ii] = q;
-  }
-  if (kES) es_factors(K.tab_i32 + K.iq_off + 12, K.Pr, K.M, pc + 4, s.sc);
-  __syncthreads();
-  // ---- HLL weights per interior face: F = w1 Xi a- + w2 Xi a+ + w3 (a+ - a-)
-  // (on warp 1, in parallel with warp 0's coefficient recurrences)
-  if (tid >= 32 && tid < 36 && !s.iarr[I_WALL + tid - 32] && part_has_face(kPart, tid - 32)) {
-    const int f = tid - 32, ax = f >> 1;
-    const double *pm = s.vsrc + (2 * f) * 4, *pp = s.vsrc + (2 * f + 1) * 4;
-    double sL = fmin(pm[ax] - K.C * sqrt(pm[3]), pp[ax] - K.C * sqrt(pp[3]));
-    double sR = fmax(pm[ax] + K.C * sqrt(pm[3]), pp[ax] + K.C * sqrt(pp[3]));
-    double w1, w2, w3;
-    if (sL >= 0.0) {
-      w1 = 1.0; w2 = 0.0; w3 = 0.0;
-    } else if (sR <= 0.0) {
-      w1 = 0.0; w2 = 1.0; w3 = 0.0;
-    } else {
-      double inv = 1.0 / (sR - sL);
-      w1 = sR * inv; w2 = -sL * inv; w3 = sL * sR * inv;
-    }
-    s.sc[S_W + 3 * f] = w1;
-    s.sc[S_W + 3 * f + 1] = w2;
-    s.sc[S_W + 3 * f + 2] = w3;
-  }
-  setup_coeffs(K, s);
   __syncthreads();
   // ---- batch A: face states -> cell basis, cell -> wall bases, r -> cell basis (result in VB)
   transform_batch(K, s, s.VA, s.VB);
