@@ -174,7 +174,7 @@ def nmom(M):
 # DRAM bytes (read + write) per FS launch, averaged over the 11 FS launches of one V-cycle of
 # the 256x256 M=10 workload, from one ncu capture of the current sweep kernels (one-CTA and
 # two-CTA cluster sweeps); no figure for the other workloads
-FS_TRAFFIC_BYTES_PER_LAUNCH = {"lid256": 392.5e6}
+FS_TRAFFIC_BYTES_PER_LAUNCH = {"lid256": 393.3e6}
 
 LEARNED_KEYS = ("status", "cycles", "final_cycles", "wasted_cycles", "rel_res", "rel_res_after_climb",
                 "coarse_cycles", "t_coarse", "t_climb", "t_final", "t_total", "climb")
