@@ -612,9 +612,11 @@ nrmg_status residual(nrmg_ctx *ctx, int level, int mode, double *out, int out_st
   return NRMG_OK;
 }
 
-nrmg_status norm_of(nrmg_ctx *ctx, int level, double *out_dev_R, double *norm_host) {
+// write_defect: the same residual evaluation also leaves L.D = r - R(f) (the mixed smoother's
+// defect of this state)
+nrmg_status norm_of(nrmg_ctx *ctx, int level, double *out_dev_R, double *norm_host, bool write_defect = false) {
   int g = 0;
-  nrmg_status s = residual(ctx, level, kResOut, out_dev_R, ctx->N, &g);
+  nrmg_status s = residual(ctx, level, write_defect ? kResDefectNorm : kResOut, out_dev_R, ctx->N, &g);
   if (s != NRMG_OK) return s;
   CK(launch_reduce_norm(ctx->partials, g, 1.0 / (ctx->grid.lx * ctx->grid.ly), ctx->dscal, ctx->stream));
   ctx->launches += 1;
@@ -1140,8 +1142,11 @@ nrmg_status nrmg_residual(nrmg_ctx *ctx, int level, double *dev_R_out, double *n
   return residual(ctx, level, kResOut, dev_R_out, ctx->N, nullptr);
 }
 
-nrmg_status nrmg_fas_cycle(nrmg_ctx *ctx, double *rel_res_out) {
-  if (!ctx) return NRMG_ERR_ARG;
+namespace {
+// One cycle of the finest level, the mass correction and the norm.  defect_fresh: the finest
+// level's D holds r - R(f) of the current state (the previous norm of this solve left it);
+// write_defect: the closing norm leaves it for the next cycle.
+nrmg_status fas_cycle(nrmg_ctx *ctx, double *rel_res_out, bool defect_fresh, bool write_defect) {
   const int K = ctx->levels - 1;
   nrmg_status s;
   ctx->lev[K].has_r = 0;
@@ -1149,12 +1154,18 @@ nrmg_status nrmg_fas_cycle(nrmg_ctx *ctx, double *rel_res_out) {
     if ((s = norm_of(ctx, K, nullptr, &ctx->res0)) != NRMG_OK) return s;
     ctx->have_res0 = 1;
   }
-  if ((s = nmg(ctx, K)) != NRMG_OK) return s;
+  if ((s = nmg(ctx, K, defect_fresh)) != NRMG_OK) return s;
   if ((s = mass_correct(ctx)) != NRMG_OK) return s;
   double r = 0.0;
-  if ((s = norm_of(ctx, K, nullptr, &r)) != NRMG_OK) return s;
+  if ((s = norm_of(ctx, K, nullptr, &r, write_defect)) != NRMG_OK) return s;
   if (rel_res_out) *rel_res_out = ctx->res0 > 0.0 ? r / ctx->res0 : 0.0;
   return NRMG_OK;
+}
+}  // namespace
+
+nrmg_status nrmg_fas_cycle(nrmg_ctx *ctx, double *rel_res_out) {
+  if (!ctx) return NRMG_ERR_ARG;
+  return fas_cycle(ctx, rel_res_out, false, false);
 }
 
 // ------------------------------------------------------------------ learned coarse-level correction
@@ -1308,11 +1319,14 @@ nrmg_status nrmg_solve(nrmg_ctx *ctx, double tol, int max_cycles, int *cycles_ou
   ctx->lev[K].has_r = 0;
   double rr = 0.0;
   nrmg_status s;
+  // precision 1: every norm of the solve also leaves the defect of its state, which the next
+  // cycle's first finest-level smoothing takes instead of evaluating it again
+  const bool mixed = ctx->opts.precision == 1;
   if (ctx->ref_fixed) {
-    if ((s = norm_of(ctx, K, nullptr, &rr)) != NRMG_OK) return s;
+    if ((s = norm_of(ctx, K, nullptr, &rr, mixed)) != NRMG_OK) return s;
     rr = ctx->res0 > 0.0 ? rr / ctx->res0 : 0.0;
   } else {
-    if ((s = norm_of(ctx, K, nullptr, &ctx->res0)) != NRMG_OK) return s;
+    if ((s = norm_of(ctx, K, nullptr, &ctx->res0, mixed)) != NRMG_OK) return s;
     ctx->have_res0 = 1;
     rr = ctx->res0 > 0.0 ? 1.0 : 0.0;
   }
@@ -1324,7 +1338,7 @@ nrmg_status nrmg_solve(nrmg_ctx *ctx, double tol, int max_cycles, int *cycles_ou
   ctx->mixed_stalled = 0;
   int it = 0;
   while (rr > tol && it < max_cycles) {
-    if ((s = nrmg_fas_cycle(ctx, &rr)) != NRMG_OK) break;
+    if ((s = fas_cycle(ctx, &rr, mixed, mixed)) != NRMG_OK) break;
     ++it;
     if (ctx->opts.precision == 1 && !ctx->mixed_off) {
       const double b = it == 1 ? rr : std::min(rr, best[(it - 1) % (kStallWindow + 1)]);

@@ -17,7 +17,7 @@ constexpr int kThreads = 256;
 constexpr int kStOk = 0, kStNonPhysical = 4, kStTimeout = 6;
 
 // Kernel modes of the Jacobi-style residual kernel.
-enum ResMode { kResOut = 0, kResDefect = 1, kResCoarseRhs = 2 };
+enum ResMode { kResOut = 0, kResDefect = 1, kResCoarseRhs = 2, kResDefectNorm = 3 };
 
 struct LevelDev {
   int nx, ny, ncell;

@@ -863,7 +863,8 @@ __global__ void __launch_bounds__(kThreads) fs_batch_kernel(const BatchDesc *des
 
 // ------------------------------------------------------------------ residual of every cell
 // mode kResOut: out[c*stride + o] = R - r and the weighted norm partials;
-// kResDefect: D = -(R - r); kResCoarseRhs: rF = R + rF (the level has no r during the call).
+// kResDefect: D = -(R - r); kResCoarseRhs: rF = R + rF (the level has no r during the call);
+// kResDefectNorm: D = -(R - r) and the norm partials.
 template <bool kES>
 __global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L, int mode, double *out,
                                                             int out_stride, double *partials) {
@@ -876,13 +877,16 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(Consts K, LevelDev L
   for (int c = blockIdx.x; c < L.ncell; c += gridDim.x) {
     const int i = c % L.nx, j = c / L.nx;
     double loc = 0.0;
-    if (mode == kResOut) {
+    if (mode == kResOut || mode == kResDefectNorm) {
       cell_residual<false, false, kES>(K, L, s, i, j, [&](int o, double Rr) {
-        if (out) out[(size_t)c * out_stride + o] = Rr;
+        if (mode == kResDefectNorm)
+          L.D[(size_t)c * NP + o] = -Rr;
+        else if (out)
+          out[(size_t)c * out_stride + o] = Rr;
         double w = s.fact[o] * s.sc[S_TPOW + s.tdeg[o]];
         loc += w * Rr * Rr;
       });
-      if (out)  // planar: the rows with odd alpha_3 are exactly zero
+      if (out && mode == kResOut)  // planar: the rows with odd alpha_3 are exactly zero
         for (int o = tid; o < K.N; o += kThreads)
           if (s.tal[2 * K.N + o] & 1) out[(size_t)c * out_stride + o] = 0.0;
       double t = block_sum(loc, s.sc + S_RED);
