@@ -138,13 +138,13 @@ nrmg_status nrmg_set_state_from_fields(nrmg_ctx *ctx, const double *dev_fields);
  * an odd finest grid). */
 size_t nrmg_learned_cycle_workspace_bytes(const nrmg_ctx *ctx);
 
-/* Which residual decides whether the correction is kept: right after the update (both
- * candidates before the post-smoothing), after the post-smoothing (each candidate smoothed
- * s2 times; the cheaper test leaves high-frequency defects of a correction to the judge, which
- * the smoother would remove), or none (the correction is always kept). */
-#define NRMG_JUDGE_UPDATE 0
-#define NRMG_JUDGE_SMOOTHED 1
-#define NRMG_JUDGE_NONE 2
+/* Acceptance rule of the correction, i.e. which residual decides whether it is kept: right
+ * after the update (both candidates before the post-smoothing), after the post-smoothing (each
+ * candidate smoothed s2 times; the cheaper rule also counts high-frequency defects of a
+ * correction that the smoother would remove), or none (the correction is always kept). */
+#define NRMG_ACCEPT_UPDATE 0
+#define NRMG_ACCEPT_SMOOTHED 1
+#define NRMG_ACCEPT_ALWAYS 2
 
 /* One cycle as nrmg_fas_cycle (Algorithm 2 on the finest level with gamma coarse cycles, then
  * the mass correction), with a learned correction of the finest level's update:
@@ -153,7 +153,7 @@ size_t nrmg_learned_cycle_workspace_bytes(const nrmg_ctx *ctx);
  *   dev_y      used when net is NULL: a given correction [H*W][10] in the network's output
  *              units (tests and bounds on what a correction can gain); NULL with net NULL =
  *              the plain update (the cycle is then nrmg_fas_cycle's, bit for bit);
- *   judge      NRMG_JUDGE_UPDATE, NRMG_JUDGE_SMOOTHED or NRMG_JUDGE_NONE;
+ *   accept_rule  NRMG_ACCEPT_UPDATE, NRMG_ACCEPT_SMOOTHED or NRMG_ACCEPT_ALWAYS;
  *   Kn, U      the problem's Knudsen number and lid speed (the input scaling);
  *   dev_ws     caller-owned device workspace, 256-byte aligned, ws_bytes >=
  *              nrmg_learned_cycle_workspace_bytes;
@@ -162,9 +162,9 @@ size_t nrmg_learned_cycle_workspace_bytes(const nrmg_ctx *ctx);
  *   scale_out  (host, may be NULL) receives s;
  *   accepted_out (host, may be NULL) receives 1 when the network's correction was kept;
  *   rel_res_out as for nrmg_fas_cycle.
- * Synchronizes.  NRMG_ERR_ARG for a one-level context, a bad workspace or judge, or a network
+ * Synchronizes.  NRMG_ERR_ARG for a one-level context, a bad workspace or acceptance rule, or a network
  * of the wrong shape or stream. */
-nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *dev_y, int judge, double Kn, double U,
+nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *dev_y, int accept_rule, double Kn, double U,
                                    void *dev_ws, size_t ws_bytes, float *dev_x_out, double *dev_fine_out,
                                    double *scale_out, int *accepted_out, double *rel_res_out);
 

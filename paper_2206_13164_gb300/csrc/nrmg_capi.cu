@@ -1216,11 +1216,11 @@ static nrmg_status copy_state(nrmg_ctx *ctx, double *dP, double *dF, double *dtp
   return NRMG_OK;
 }
 
-nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *dev_y, int judge, double Kn, double U,
+nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *dev_y, int accept_rule, double Kn, double U,
                                    void *dev_ws, size_t ws_bytes, float *dev_x_out, double *dev_fine_out,
                                    double *scale_out, int *accepted_out, double *rel_res_out) {
   if (!ctx || !dev_ws || ((uintptr_t)dev_ws & 255) != 0 || !(Kn > 0.0) || !(U > 0.0)) return NRMG_ERR_ARG;
-  if (judge != NRMG_JUDGE_UPDATE && judge != NRMG_JUDGE_SMOOTHED && judge != NRMG_JUDGE_NONE) return NRMG_ERR_ARG;
+  if (accept_rule != NRMG_ACCEPT_UPDATE && accept_rule != NRMG_ACCEPT_SMOOTHED && accept_rule != NRMG_ACCEPT_ALWAYS) return NRMG_ERR_ARG;
   const size_t need = nrmg_learned_cycle_workspace_bytes(ctx);
   if (need == 0 || ws_bytes < need) return NRMG_ERR_ARG;
   const int K = ctx->levels - 1;
@@ -1258,12 +1258,12 @@ nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *de
       y = w.y;
     }
     double r_plain = 0.0, r_net = 0.0;
-    if (judge == NRMG_JUDGE_UPDATE && (s = norm_of(ctx, K, nullptr, &r_plain)) != NRMG_OK) return s;
+    if (accept_rule == NRMG_ACCEPT_UPDATE && (s = norm_of(ctx, K, nullptr, &r_plain)) != NRMG_OK) return s;
     if ((s = copy_state(ctx, w.bP, w.bF, w.btp, Lf.P, Lf.F, Lf.tp)) != NRMG_OK) return s;  // the plain update
     CK(launch_field_correct(ctx->K, Lf, y, w.s, U, grid_for(ctx, 3, Lf.ncell), st));
     ctx->launches += 1;
     bool physical = true;
-    if (judge == NRMG_JUDGE_UPDATE) {
+    if (accept_rule == NRMG_ACCEPT_UPDATE) {
       s = norm_of(ctx, K, nullptr, &r_net);  // a non-physical candidate reports here (status cleared)
       if (s != NRMG_OK && s != NRMG_ERR_NONPHYSICAL) return s;
       physical = s == NRMG_OK;
@@ -1272,7 +1272,7 @@ nrmg_status nrmg_fas_cycle_learned(nrmg_ctx *ctx, nrmg_net *net, const float *de
       if ((s = sync_status(ctx)) != NRMG_OK && s != NRMG_ERR_NONPHYSICAL) return s;
       physical = s == NRMG_OK;
       accepted = physical;
-      if (physical && judge == NRMG_JUDGE_SMOOTHED) {
+      if (physical && accept_rule == NRMG_ACCEPT_SMOOTHED) {
         // smooth the candidate, keep it aside, smooth the plain update, compare
         s = smooth_level(ctx, K, o.s2);
         if (s == NRMG_OK) s = norm_of(ctx, K, nullptr, &r_net);

@@ -35,7 +35,7 @@ from .nrmg import Batch, NrmgError, Solver
 
 CIN, COUT = 19, 10          # NRMG_LEARN_CIN, NRMG_LEARN_COUT
 CORR_CIN = 29               # NRMG_CORR_CIN
-JUDGE_UPDATE, JUDGE_SMOOTHED, JUDGE_NONE = 0, 1, 2  # NRMG_JUDGE_*
+ACCEPT_UPDATE, ACCEPT_SMOOTHED, ACCEPT_ALWAYS = 0, 1, 2  # NRMG_ACCEPT_*
 HIDDEN = 64
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "lid_net.npz")
 CORR_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "corr_net.npz")
@@ -217,8 +217,8 @@ class LearnedCycle:
     when it lowers the residual norm right after the update.  net=None runs the plain cycle
     (and still forms the network input, for training data)."""
 
-    def __init__(self, solver: Solver, Kn: float, U: float, judge: int = JUDGE_UPDATE):
-        self.s, self.Kn, self.U, self.judge = solver, Kn, U, judge
+    def __init__(self, solver: Solver, Kn: float, U: float, rule: int = ACCEPT_UPDATE):
+        self.s, self.Kn, self.U, self.rule = solver, Kn, U, rule
         self.L = _lib()
         nbytes = self.L.nrmg_learned_cycle_workspace_bytes(solver.ctx)
         if nbytes == 0:
@@ -228,13 +228,13 @@ class LearnedCycle:
         self.accepted = 0
         self.cycles = 0
 
-    def cycle(self, net=None, x_out=None, fine_out=None, y=None, judge=None):
+    def cycle(self, net=None, x_out=None, fine_out=None, y=None, rule=None):
         """One cycle: (relative residual, correction kept, scale s of the coarse change).
         y: a given correction [H, W, 10] (network units) when net is None."""
         rel, acc, sc = c_double(0.0), c_int(0), c_double(0.0)
-        judge = self.judge if judge is None else judge
+        rule = self.rule if rule is None else rule
         st = self.L.nrmg_fas_cycle_learned(self.s.ctx, net.h if net is not None else None,
-                                           _p(y.contiguous(), torch.float32) if y is not None else None, judge,
+                                           _p(y.contiguous(), torch.float32) if y is not None else None, rule,
                                            self.Kn, self.U, c_void_p(self.ws.data_ptr()), self.nbytes,
                                            _p(x_out, torch.float32) if x_out is not None else None,
                                            _p(fine_out, torch.float64) if fine_out is not None else None,
@@ -304,24 +304,25 @@ def correction_pairs(problems, N, M, ref_tol=1e-10, stop=1e-7, max_cycles=60, lo
     return torch.stack(xs), torch.stack(ts)
 
 
-def evaluate_correction(N, M, Kn, U, net, tol=1e-8, max_cycles=400, grid=0, judges=(JUDGE_UPDATE,)):
+def evaluate_correction(N, M, Kn, U, net, tol=1e-8, max_cycles=400, grid=0, rules=(ACCEPT_UPDATE,)):
     """Cycles and wall time to tol from the Maxwellian start: the plain cycle and the cycle
-    with the learned correction under each judge (\"learned\" for the first, \"learned_j<k>\"
+    with the learned correction under each acceptance rule (\"learned\" for the first,
+    \"learned_r<k>\"
     for the others), and each learned solution's largest field difference from the plain one."""
     out = {"N": N, "M": M, "Kn": Kn, "U": U}
     runs = {}
-    names = [("plain", None, JUDGE_UPDATE)] + [("learned" if k == 0 else f"learned_j{j}", net, j)
-                                               for k, j in enumerate(judges)]
+    names = [("plain", None, ACCEPT_UPDATE)] + [("learned" if k == 0 else f"learned_r{j}", net, j)
+                                               for k, j in enumerate(rules)]
     for name, nn, j in names:
         s = lid_solver(N, M, Kn, U)
         s.set_grid(grid)
-        lc = LearnedCycle(s, Kn, U, judge=j)
+        lc = LearnedCycle(s, Kn, U, rule=j)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cyc, rel, acc = lc.solve(nn, tol, max_cycles)
         torch.cuda.synchronize()
         runs[name] = s
-        out[name] = {"cycles": cyc, "rel_res": rel, "kept": acc, "judge": j, "seconds": time.perf_counter() - t0}
+        out[name] = {"cycles": cyc, "rel_res": rel, "kept": acc, "rule": j, "seconds": time.perf_counter() - t0}
     fp = runs["plain"].fields()
     for name, s in runs.items():
         if name != "plain":
@@ -645,7 +646,7 @@ def main(argv=None):
         del X, T
         ev = evaluate_correction(a.eval_N, a.M, a.holdout[0], a.holdout[1],
                                  Net.load(a.out, max_pixels=a.eval_N * a.eval_N),
-                                 judges=(JUDGE_UPDATE, JUDGE_SMOOTHED, JUDGE_NONE))
+                                 rules=(ACCEPT_UPDATE, ACCEPT_SMOOTHED, ACCEPT_ALWAYS))
         print(json.dumps(ev), flush=True)
         return
     if a.cmd == "eval":
