@@ -287,6 +287,17 @@ def learned512_record(args, local_rank=0):
     del tuner
     with ClockSampler(gpu_id) as clk:
         ev = learned.evaluate(N, M, Kn, U, net, start=64, grid=grid, mixed=True)
+    # the learned coarse-level correction on its held-out cavity (128x128, M = 8: the network
+    # was trained on 64x64, M = 8 trajectories), plain cycle against the cycle with the
+    # correction under the update-residual and the post-smoothing acceptance rules
+    try:
+        cnet = learned.Net.load(learned.CORR_WEIGHTS, max_pixels=128 * 128)
+        corr = learned.evaluate_correction(128, 8, Kn, U, cnet, rules=(learned.ACCEPT_UPDATE,
+                                                                      learned.ACCEPT_SMOOTHED))
+        corr["weights"] = os.path.relpath(learned.CORR_WEIGHTS, ROOT)
+        del cnet
+    except Exception as e:  # the record of the learned start stands without it
+        corr = {"error": f"{type(e).__name__}: {e}"}
     peak, src = bf16_peak()
     t_net, t_plain = ev["net"]["t_total"], ev["plain"]["t_total"]
     out = {"metric": "seconds to relative residual 1e-8 (learned start)", "value": t_net, "unit": "s",
@@ -306,6 +317,7 @@ def learned512_record(args, local_rank=0):
            "net_mixed": {k: ev["net_mixed"][k] for k in LEARNED_KEYS + ("max_field_diff", "field_rel_err")},
            "speedup_vs_plain": t_plain / t_net,
            "speedup_vs_plain_with_mixed_smoother": t_plain / ev["net_mixed"]["t_total"],
+           "coarse_correction": corr,
            "roofline": {"bound": "tensor", "kernel": "network forward (4 conv3x3 launches, mma.sync BF16)",
                         "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,
                         "traffic": None, "peak_source": src, "forward_ms": fwd_ms,

@@ -307,8 +307,8 @@ def correction_pairs(problems, N, M, ref_tol=1e-10, stop=1e-7, max_cycles=60, lo
 def evaluate_correction(N, M, Kn, U, net, tol=1e-8, max_cycles=400, grid=0, rules=(ACCEPT_UPDATE,)):
     """Cycles and wall time to tol from the Maxwellian start: the plain cycle and the cycle
     with the learned correction under each acceptance rule (\"learned\" for the first,
-    \"learned_r<k>\"
-    for the others), and each learned solution's largest field difference from the plain one."""
+    \"learned_r<k>\" for the others), and each learned solution's largest field difference
+    from the plain one."""
     out = {"N": N, "M": M, "Kn": Kn, "U": U}
     runs = {}
     names = [("plain", None, ACCEPT_UPDATE)] + [("learned" if k == 0 else f"learned_r{j}", net, j)
